@@ -1,0 +1,217 @@
+/*
+ * raygs.h -- C ABI of the GB300 (sm_103a) renderer for ray-based Gaussian splatting.
+ *
+ * The library renders the RayGS image of Sec. 3.2 (Eq. Q_ray, Eq. rend_opacity,
+ * Eq. rendering) of "Hardware-Rasterized Ray-Based Gaussian Splatting" (arXiv 2503.18682),
+ * with the paper's per-primitive vertex stage (Sec. 4.1: the smallest enclosing 3D quad,
+ * Eq. V_ray) used to bin primitives into screen tiles, its fragment formula (Sec. 4.2,
+ * App. A.4) evaluated per pixel, and the approximate anti-aliasing of Sec. 5 (Eq. mip).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Ownership: the caller allocates every buffer.  Device buffers (marked "device") are
+ *    read or written by kernels; the library never calls cudaMalloc/cudaFree.  Host-side
+ *    plan objects are the only thing the library allocates (plain malloc/new).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work is enqueued on it asynchronously; no entry point synchronises unless
+ *    its comment says so.
+ *  - Errors: every entry point returns a raygs_status and never aborts or throws.
+ *    RAYGS_ERR_INVALID_ARG is returned before any work is enqueued.  RAYGS_ERR_CUDA means a
+ *    CUDA call failed; raygs_last_cuda_error() returns its cudaError_t.  Conditions found
+ *    on the device (instance capacity exceeded, non-finite attributes) are recorded in
+ *    device counters and reported by raygs_read_counters().
+ *  - Camera model: pinhole (Sec. 3.1), OpenCV axes (x right, y down, z forward),
+ *    x_cam = R x_world + t; pixel (i, j) is the ray ((i+0.5-cx)/fx, (j+0.5-cy)/fy, 1).
+ *  - Primitive parameters (Sec. 3, "Scene representation"): mean, rotation quaternion
+ *    (w, x, y, z; normalised internally), log of the diagonal scale, opacity logit
+ *    (o = sigmoid), colour as spherical-harmonic coefficients whose first coefficient is
+ *    the base RGB colour (rgb = max(0, k_0 + sum_{l>=1} Y_lm(d) k_lm), real SH without the
+ *    Condon-Shortley phase, d = unit vector from the camera centre to the mean, world frame).
+ *  - Image outputs are float32, views concatenated in order; view v starts at pixel
+ *    raygs_plan_pixel_offset(plan, v) and is row-major [H][W].
+ */
+#ifndef RAYGS_H
+#define RAYGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RAYGS_MAX_VIEWS 64
+
+typedef enum {
+  RAYGS_OK = 0,
+  RAYGS_ERR_INVALID_ARG = 1, /* null pointer, bad size or dtype, misaligned buffer, ... */
+  RAYGS_ERR_CAPACITY = 2,    /* workspace too small for the plan */
+  RAYGS_ERR_CUDA = 3,        /* a CUDA runtime call failed (see raygs_last_cuda_error) */
+  RAYGS_ERR_STATE = 4        /* call out of order (e.g. render before bin_sort) */
+} raygs_status;
+
+typedef enum { RAYGS_F32 = 0, RAYGS_F16 = 1, RAYGS_BF16 = 2 } raygs_dtype;
+
+/* Primitive set S of Sec. 3 ("Scene representation"), structure of arrays, device memory.
+ * Every pointer must be 16-byte aligned. */
+typedef struct {
+  int64_t n;                  /* number of primitives, 0 <= n < 2^31 */
+  const float *means;         /* [n][3] float32, world frame */
+  const void *log_scales;     /* [n][3] in scale_dtype */
+  const float *quats;         /* [n][4] float32 (w, x, y, z), any nonzero norm */
+  const void *opacity_logits; /* [n] in opacity_dtype */
+  const void *sh;             /* [n][K][3] in sh_dtype, K = (sh_degree + 1)^2 */
+  int32_t sh_degree;          /* 0..3 */
+  int32_t scale_dtype;        /* raygs_dtype: F32, F16 or BF16 */
+  int32_t opacity_dtype;      /* raygs_dtype: F32 or F16 */
+  int32_t sh_dtype;           /* raygs_dtype: F32, F16 or BF16 */
+} raygs_scene;
+
+/* One pinhole view (Sec. 3.1).  mip != 0 applies the anti-aliasing filter of Sec. 5. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height; /* 1 .. 32768 each */
+  float R[9];            /* world -> camera rotation, row-major */
+  float t[3];
+  float near_z;          /* primitives whose centre depth is <= near_z are culled (Sec. 4.1) */
+  int32_t mip;
+} raygs_camera;
+
+/* Renderer settings.  raygs_config_default() fills the documented defaults. */
+typedef struct {
+  float p_min;            /* support cut-off of Eq. support (default 1/255) */
+  float t_stop;           /* compositing stops before T would drop below this (1e-4) */
+  float alpha_max;        /* rendered opacity clamp (0.99) */
+  float mip_sigma2;       /* sigma^2 of Sec. 5 in pixel^2 at unit distance (0.1) */
+  int32_t tile_w, tile_h; /* screen tile in pixels: 16x16 (default), 16x8, 32x16 or 8x8 */
+  int32_t fp64_degenerate; /* 1: FP64 vertex stage for primitives whose scale ratio
+                              max/min exceeds degenerate_ratio (default 1) */
+  float degenerate_ratio; /* 1e3 */
+} raygs_config;
+
+/* Device-side counters of the last preprocess / bin_sort / render sequence. */
+typedef struct {
+  int64_t n_visible;    /* (primitive, view) pairs that survived culling */
+  int64_t n_instances;  /* (primitive, tile) instances emitted (may exceed capacity) */
+  int64_t capacity;     /* instance capacity of the plan */
+  int64_t n_nonfinite;  /* primitives culled because an attribute was NaN/Inf */
+  int32_t overflow;     /* 1 when n_instances > capacity: the image is incomplete */
+} raygs_counters;
+
+/* Reference-gradient outputs of raygs_render_backward: float32 device buffers laid out
+ * like the matching scene attributes.  Any pointer may be NULL to skip that gradient. */
+typedef struct {
+  float *d_means;          /* [n][3] */
+  float *d_log_scales;     /* [n][3] */
+  float *d_quats;          /* [n][4]  (gradient w.r.t. the un-normalised quaternion) */
+  float *d_opacity_logits; /* [n] */
+  float *d_sh;             /* [n][K][3] */
+} raygs_grads;
+
+typedef struct raygs_plan raygs_plan;
+
+/* ---------------------------------------------------------------- configuration */
+
+/* Fill *cfg with the defaults listed in raygs_config. */
+void raygs_config_default(raygs_config *cfg);
+
+/* Human-readable name of a status code (static string). */
+const char *raygs_status_string(raygs_status s);
+
+/* cudaError_t of the last failed CUDA call in this thread (0 if none). */
+int raygs_last_cuda_error(void);
+
+/* ---------------------------------------------------------------- plan / workspace */
+
+/*
+ * Create a plan for rendering `n_views` cameras (1..RAYGS_MAX_VIEWS) of a scene with
+ * `n_gaussians` primitives, with room for `max_instances` (primitive, tile) pairs.
+ * Host-side only; the cameras are copied.  Returns INVALID_ARG for bad sizes/config.
+ */
+raygs_status raygs_plan_create(const raygs_camera *cams, int32_t n_views, int64_t n_gaussians,
+                               int64_t max_instances, const raygs_config *cfg,
+                               raygs_plan **out);
+
+/* Release a plan (host memory only; the caller frees its workspace). NULL is a no-op. */
+void raygs_plan_destroy(raygs_plan *plan);
+
+/* Bytes of device workspace the plan needs (256-byte aligned start required). */
+size_t raygs_plan_workspace_bytes(const raygs_plan *plan);
+
+/* Attach a caller-owned device workspace of at least raygs_plan_workspace_bytes() bytes
+ * and upload the cameras (synchronous H2D copy on the default stream; not for the hot path).
+ * Returns CAPACITY if `bytes` is too small, INVALID_ARG if misaligned. */
+raygs_status raygs_plan_bind(raygs_plan *plan, void *workspace, size_t bytes);
+
+/* Replace the camera poses (R, t) of all views; sizes and intrinsics must not change.
+ * Enqueued as an async H2D copy on `stream` from host memory the library owns. */
+raygs_status raygs_plan_set_poses(raygs_plan *plan, const raygs_camera *cams, void *stream);
+
+int64_t raygs_plan_num_pixels(const raygs_plan *plan);          /* sum of W*H over views */
+int64_t raygs_plan_pixel_offset(const raygs_plan *plan, int32_t view);
+int64_t raygs_plan_num_tiles(const raygs_plan *plan);           /* screen tiles, all views */
+
+/* ---------------------------------------------------------------- hot path */
+
+/*
+ * Per-primitive vertex stage for every view (Sec. 3 activation; Sec. 3.2 Eq. c skip;
+ * Sec. 5 Eq. mip; Sec. 4.1 and App. A.1-A.3 quad V_ray -> screen tile rectangle; the
+ * per-pixel factors of the fragment formula of Sec. 4.2 / App. A.4; colour from SH).
+ * Reads the scene, writes per-(primitive, view) depth keys, tile rectangles and 64-byte
+ * pixel records into the workspace.  Requires a bound plan and scene->n == n_gaussians.
+ */
+raygs_status raygs_preprocess(raygs_plan *plan, const raygs_scene *scene, void *stream);
+
+/*
+ * Binning for Eq. rendering's depth order: stable on-device radix sort of the visible
+ * (primitive, view) pairs by float32 centre depth (ties keep primitive order), emission of
+ * one instance per covered tile in that order, stable radix sort of instances by tile id,
+ * and per-tile [start, end) ranges.  Requires raygs_preprocess on the same stream first.
+ */
+raygs_status raygs_bin_sort(raygs_plan *plan, void *stream);
+
+/*
+ * Per-tile rasterisation: for every pixel, the ray-maximum divergence D_ray in closed form
+ * (Sec. 4.2 fragment formula with the quad coordinate obtained from the pixel ray),
+ * omega = min(alpha_max, o exp(-D/2)) when D <= kappa (Eq. rend_opacity, Eq. support), and
+ * front-to-back compositing (Eq. rendering) stopping before T < t_stop.
+ *   rgb       [num_pixels][3] float32 device, required
+ *   T_final   [num_pixels]    float32 device, optional (NULL): final transmittance
+ *   n_contrib [num_pixels]    int32 device, optional (NULL): 1 + position of the last
+ *             composited instance in the pixel's tile list (0 if none); needed by backward
+ */
+raygs_status raygs_render(raygs_plan *plan, float *rgb, float *T_final, int32_t *n_contrib,
+                          void *stream);
+
+/*
+ * Gradients of a scalar loss L through raygs_render back to the scene parameters
+ * (not in the paper, whose renderer is not differentiable).  Uses the workspace of the
+ * preceding forward pass (same plan, scene unchanged).  dL_drgb [num_pixels][3] device
+ * required; dL_dT [num_pixels] optional.  T_final and n_contrib are the forward outputs.
+ * Gradient buffers are overwritten (not accumulated).
+ */
+raygs_status raygs_render_backward(raygs_plan *plan, const raygs_scene *scene,
+                                   const float *T_final, const int32_t *n_contrib,
+                                   const float *dL_drgb, const float *dL_dT,
+                                   const raygs_grads *grads, void *stream);
+
+/* Synchronise `stream` and read the device counters of the last sequence. */
+raygs_status raygs_read_counters(raygs_plan *plan, raygs_counters *out, void *stream);
+
+/* ---------------------------------------------------------------- batching */
+
+/*
+ * Capture raygs_preprocess + raygs_bin_sort + raygs_render for this plan, scene and
+ * outputs into a CUDA graph held by the plan (replaces a previous one).  The scene and
+ * output pointers are baked in; their contents may change between launches.
+ */
+raygs_status raygs_graph_capture(raygs_plan *plan, const raygs_scene *scene, float *rgb,
+                                 float *T_final, int32_t *n_contrib, void *stream);
+
+/* Launch the captured graph on `stream`. */
+raygs_status raygs_graph_launch(raygs_plan *plan, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAYGS_H */

@@ -1,0 +1,474 @@
+// Per-primitive vertex stage (Sec. 3, Sec. 3.2, Sec. 4.1, Sec. 5 of the paper) for every
+// view of a batch.  One thread per primitive loops over the views; attributes are staged
+// once per CTA with 16-byte coalesced loads and converted to float32 in shared memory.
+//
+// Outputs per (view v, primitive g), index v*N + g:
+//   depth_key  float32 bits of the view-space centre depth, or kCulled
+//   rect       inclusive screen-tile rectangle covered by the projected quad (Eq. V_ray)
+//   rec        64-byte pixel record (see Rec): the factors of the fragment formula of
+//              Sec. 4.2 / App. A.4 in a form that is evaluated from the pixel ray
+//
+// Primitives whose scale ratio exceeds degenerate_ratio are skipped by the float32
+// kernel and handled by preprocess_fp64_kernel, which runs the same stage in FP64.
+#include "raygs_internal.cuh"
+
+namespace raygs {
+
+
+constexpr int kPrepThreads = 128;
+
+__device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double t_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float t_log(float x) { return logf(x); }
+__device__ __forceinline__ double t_log(double x) { return log(x); }
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+
+// Rotation of a quaternion (w, x, y, z) after normalisation, closed-form matrix.
+template <typename T>
+__device__ __forceinline__ void quat_rot(T w, T x, T y, T z, T R[9]) {
+  T inv = T(1) / t_sqrt(w * w + x * x + y * y + z * z);
+  w *= inv; x *= inv; y *= inv; z *= inv;
+  R[0] = T(1) - T(2) * (y * y + z * z); R[1] = T(2) * (x * y - w * z); R[2] = T(2) * (x * z + w * y);
+  R[3] = T(2) * (x * y + w * z); R[4] = T(1) - T(2) * (x * x + z * z); R[5] = T(2) * (y * z - w * x);
+  R[6] = T(2) * (x * z - w * y); R[7] = T(2) * (y * z + w * x); R[8] = T(1) - T(2) * (x * x + y * y);
+}
+
+struct StageOut {
+  float G[4], h[2], kp, c2h, lo2o;
+  int tx0, ty0, tx1, ty1;
+};
+
+// The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
+// rotation; s: scales; o: prior opacity.  Returns false when the primitive is skipped or
+// covers no pixel of this view.
+template <typename T>
+__device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, const DevCam &cam,
+                           float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out) {
+  // R_c = R_wc R_p: columns n_k are the primitive's axes in the camera frame.
+  T Rc[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Rc[3 * i + j] = T(cam.R[3 * i]) * Rp[j] + T(cam.R[3 * i + 1]) * Rp[3 + j] +
+                      T(cam.R[3 * i + 2]) * Rp[6 + j];
+  T pk[3], s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    pk[k] = Rc[k] * mu[0] + Rc[3 + k] * mu[1] + Rc[6 + k] * mu[2];  // n_k . mu
+    s[k] = s_in[k];
+  }
+  if (cam.mip) {
+    // Sec. 5, Eq. mip: Sigma^ = Sigma + lam I with lam = sigma^2 |mu|^2 / (fx fy); the
+    // opacity is modulated by sqrt(|Sigma| c^2 / (|Sigma^| c^^2)).
+    T lam = T(mip_sigma2) * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) /
+            (T(cam.fx) * T(cam.fy));
+    T c2 = 0, c2h = 0, ratio = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T s2 = s[k] * s[k], s2h = s2 + lam;
+      c2 += pk[k] * pk[k] / s2;
+      c2h += pk[k] * pk[k] / s2h;
+      ratio *= s2 / s2h;
+      s[k] = t_sqrt(s2h);
+    }
+    o *= t_sqrt(ratio * c2 / c2h);
+  }
+  // Eq. support: kappa = -2 log(p_min / o); skip when kappa <= 0.
+  T kappa = T(2) * t_log(o / T(p_min));
+  if (!(kappa > T(0))) return false;
+
+  // Conservative frustum test: every supported ray passes within sqrt(kappa) s_max of mu.
+  {
+    T smax = fmax(fmax(s[0], s[1]), s[2]);
+    T rad = t_sqrt(kappa) * smax * T(1.001) + T(1e-6);
+    if (mu[0] - T(cam.xmin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.xmin) * T(cam.xmin))) return false;
+    if (T(cam.xmax) * mu[2] - mu[0] < -rad * t_sqrt(T(1) + T(cam.xmax) * T(cam.xmax))) return false;
+    if (mu[1] - T(cam.ymin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.ymin) * T(cam.ymin))) return false;
+    if (T(cam.ymax) * mu[2] - mu[1] < -rad * t_sqrt(T(1) + T(cam.ymax) * T(cam.ymax))) return false;
+  }
+
+  // Sec. 3.2 Eq. c: c^2 = mu^T Sigma^-1 mu = |S^-1 R^T mu|^2; skip when c^2 <= kappa.
+  T m[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) m[k] = pk[k] / s[k];
+  T c2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+  if (!(c2 > kappa)) return false;
+  T c = t_sqrt(c2);
+
+  // ---- Sec. 4.1 quad.  mu^ = S^-1 R^T mu / c; R_{mu^<-v} of App. A.1 (columns 0, 1).
+  T mh0 = m[0] / c, mh1 = m[1] / c, mh2 = m[2] / c;
+  bool up = mh2 >= T(0);
+  T a0 = mh0, a1 = mh1, a2 = up ? mh2 + T(1) : mh2 - T(1);
+  T inv = T(2) / (a0 * a0 + a1 * a1 + a2 * a2);
+  T r0[3] = {inv * a0 * a0 - T(1), inv * a1 * a0, inv * a2 * a0};
+  T r1[3] = {inv * a0 * a1, inv * a1 * a1 - T(1), inv * a2 * a1};
+  if (!up) { r0[0] = -r0[0]; r0[1] = -r0[1]; r0[2] = -r0[2]; }  // times P = diag(-1,1,-1)
+  // Q_{0:2} = R S R_{mu^<-v} restricted to its first two columns (Eq. invPhi).
+  T q0[3], q1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    q0[i] = Rc[3 * i] * s[0] * r0[0] + Rc[3 * i + 1] * s[1] * r0[1] + Rc[3 * i + 2] * s[2] * r0[2];
+    q1[i] = Rc[3 * i] * s[0] * r1[0] + Rc[3 * i + 1] * s[1] * r1[1] + Rc[3 * i + 2] * s[2] * r1[2];
+  }
+  // Eq. optim2: u1 = top eigenvector of B = Q_{0:2}^T Q_{0:2} (half-angle form).
+  T B00 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+  T B01 = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2];
+  T B11 = q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2];
+  T dd = B00 - B11, rho = t_sqrt(dd * dd + T(4) * B01 * B01);
+  T u1x = T(1), u1y = T(0);
+  if (rho > T(1e-12) * (B00 + B11)) {
+    if (dd >= T(0)) { u1x = dd + rho; u1y = T(2) * B01; }
+    else { u1x = T(2) * B01; u1y = rho - dd; }
+    T un = T(1) / t_sqrt(u1x * u1x + u1y * u1y);
+    u1x *= un; u1y *= un;
+  }
+  // u0 = u1 rotated by +90 degrees; Z_ray = (sqrt(kappa)/b) O, b = sqrt(1 - kappa/c^2).
+  T zs = t_sqrt(kappa) / t_sqrt(T(1) - kappa / c2);
+  T A0[3], A1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    A0[i] = zs * (-u1y * q0[i] + u1x * q1[i]);  // Q_{0:2} u0
+    A1[i] = zs * (u1x * q0[i] + u1y * q1[i]);   // Q_{0:2} u1
+  }
+  // Eq. V_ray: vertices mu + (+-1) A0 + (+-1) A1; screen bounding box of their projections.
+  bool full = false;
+  float xmn = 3.0e38f, xmx = -3.0e38f, ymn = 3.0e38f, ymx = -3.0e38f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T sa = (k & 2) ? T(1) : T(-1), sb = (k == 1 || k == 2) ? T(1) : T(-1);
+    T px = mu[0] + sa * A0[0] + sb * A1[0];
+    T py = mu[1] + sa * A0[1] + sb * A1[1];
+    T pz = mu[2] + sa * A0[2] + sb * A1[2];
+    if (!(pz > T(1e-12))) { full = true; continue; }
+    float u = float(T(cam.fx) * px / pz + T(cam.cx));
+    float v = float(T(cam.fy) * py / pz + T(cam.cy));
+    xmn = fminf(xmn, u); xmx = fmaxf(xmx, u); ymn = fminf(ymn, v); ymx = fmaxf(ymx, v);
+  }
+  int i0, i1, j0, j1;
+  if (full) {
+    i0 = 0; j0 = 0; i1 = cam.W - 1; j1 = cam.H - 1;
+  } else {
+    if (!(xmn <= xmx) || !(ymn <= ymx)) return false;  // NaN guard
+    const float lim = 1.0e8f;
+    float mgx = 1e-3f + 1e-5f * fmaxf(fabsf(xmn), fabsf(xmx));
+    float mgy = 1e-3f + 1e-5f * fmaxf(fabsf(ymn), fabsf(ymx));
+    // pixel centre i + 0.5 inside [xmn, xmx] (with a small conservative margin)
+    float fi0 = ceilf(fminf(fmaxf(xmn - 0.5f - mgx, -lim), lim));
+    float fi1 = floorf(fminf(fmaxf(xmx - 0.5f + mgx, -lim), lim));
+    float fj0 = ceilf(fminf(fmaxf(ymn - 0.5f - mgy, -lim), lim));
+    float fj1 = floorf(fminf(fmaxf(ymx - 0.5f + mgy, -lim), lim));
+    fi0 = fmaxf(fi0, 0.f); fj0 = fmaxf(fj0, 0.f);
+    fi1 = fminf(fi1, float(cam.W - 1)); fj1 = fminf(fj1, float(cam.H - 1));
+    if (fi0 > fi1 || fj0 > fj1) return false;
+    i0 = int(fi0); i1 = int(fi1); j0 = int(fj0); j1 = int(fj1);
+  }
+  out.tx0 = i0 / tile_w; out.tx1 = i1 / tile_w;
+  out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
+
+  // ---- Per-pixel factors.  With y = K x, K = Q^-1 (App. A.4 steps g-i),
+  // D = c^2 |y01|^2 / |y|^2, which is the fragment formula 1/(c^-2 + |Z a|^-2) with the
+  // quad coordinate Z a = c U^T y01 / y2 read off the pixel ray.  The rows of K01 span the
+  // Sigma-orthonormal complement of mu, built stably from an orthonormal basis E of the
+  // plane orthogonal to mu: K01 = L^-1 E^T with L L^T = E^T Sigma E.  Since K01 mu = 0,
+  // y01 only needs the pixel offset from the projected centre.
+  T nn = t_sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
+  T n0 = mu[0] / nn, n1 = mu[1] / nn, n2 = mu[2] / nn;
+  T sg = n2 >= T(0) ? T(1) : T(-1);
+  T ba = T(-1) / (sg + n2);
+  T bb = n0 * n1 * ba;
+  T e1[3] = {T(1) + sg * n0 * n0 * ba, sg * bb, -sg * n0};
+  T e2[3] = {bb, sg + n1 * n1 * ba, -n1};
+  T M0[3], M1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    M0[k] = (e1[0] * Rc[k] + e1[1] * Rc[3 + k] + e1[2] * Rc[6 + k]) * s[k];
+    M1[k] = (e2[0] * Rc[k] + e2[1] * Rc[3 + k] + e2[2] * Rc[6 + k]) * s[k];
+  }
+  T a00 = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2];
+  T a01 = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
+  T a11 = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2];
+  T l00 = t_sqrt(a00);
+  T l10 = a01 / l00;
+  T l11 = t_sqrt(fmax(a11 - l10 * l10, a11 * T(1e-30)));
+  T f10 = l10 / l00;
+  T k0[3] = {e1[0] / l00, e1[1] / l00, e1[2] / l00};
+  T k1[3] = {(e2[0] - f10 * e1[0]) / l11, (e2[1] - f10 * e1[1]) / l11, (e2[2] - f10 * e1[2]) / l11};
+  T scl = mu[2] / c;  // normalise so that y2 = 1 on the centre ray
+  out.G[0] = float(k0[0] * T(cam.ifx) * scl);
+  out.G[1] = float(k0[1] * T(cam.ify) * scl);
+  out.G[2] = float(k1[0] * T(cam.ifx) * scl);
+  out.G[3] = float(k1[1] * T(cam.ify) * scl);
+  // y2 = mu^T Sigma^-1 x / c; Sigma^-1 mu = sum_k n_k m_k / s_k.
+  T w0 = Rc[0] * m[0] / s[0] + Rc[1] * m[1] / s[1] + Rc[2] * m[2] / s[2];
+  T w1 = Rc[3] * m[0] / s[0] + Rc[4] * m[1] / s[1] + Rc[5] * m[2] / s[2];
+  T sh = mu[2] / c2;
+  out.h[0] = float(w0 * T(cam.ifx) * sh);
+  out.h[1] = float(w1 * T(cam.ify) * sh);
+  out.kp = float((c2 - kappa) / kappa);
+  out.c2h = float(c2 * T(0.5 * 1.4426950408889634));
+  out.lo2o = float(t_log(o) * T(1.4426950408889634));
+  return true;
+}
+
+// Camera-frame mean in double-float: R mu + t with error-free products and sums.
+__device__ __forceinline__ void mean_cam_df(const DevCam &cam, float mx, float my, float mz, df out[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    df acc = {cam.t[r], 0.f};
+    acc = df_add(acc, two_prod(cam.R[3 * r], mx));
+    acc = df_add(acc, two_prod(cam.R[3 * r + 1], my));
+    acc = df_add(acc, two_prod(cam.R[3 * r + 2], mz));
+    out[r] = acc;
+  }
+}
+
+// Depth key: the fused chain fmaf(R20, x, fmaf(R21, y, fmaf(R22, z, t2))) in float32.
+__device__ __forceinline__ float depth_f32(const DevCam &cam, float mx, float my, float mz) {
+  return __fmaf_rn(cam.R[6], mx, __fmaf_rn(cam.R[7], my, __fmaf_rn(cam.R[8], mz, cam.t[2])));
+}
+
+// Real spherical harmonics (no Condon-Shortley phase) of unit direction (x, y, z) applied
+// to coefficients coef[k*3 + ch] (stride-1 floats); the first coefficient is the colour.
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float *coef, float x, float y, float z, float rgb[3]) {
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) rgb[ch] = coef[ch];
+  if (DEG >= 1) {
+    const float c1 = 0.4886025119029199f;  // sqrt(3/(4 pi))
+    float Y[3] = {c1 * y, c1 * z, c1 * x};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (1 + k) + ch], rgb[ch]);
+  }
+  if (DEG >= 2) {
+    const float c2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
+    const float c2b = 0.31539156525252005f;  // sqrt(5/(16 pi))
+    const float c2c = 0.5462742152960396f;   // sqrt(15/(16 pi))
+    float Y[5] = {c2a * x * y, c2a * y * z, c2b * (3.f * z * z - 1.f), c2a * x * z, c2c * (x * x - y * y)};
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (4 + k) + ch], rgb[ch]);
+  }
+  if (DEG >= 3) {
+    const float c3a = 0.5900435899266435f;  // sqrt(35/(32 pi))
+    const float c3b = 2.890611442640554f;   // sqrt(105/(4 pi))
+    const float c3c = 0.4570457994644658f;  // sqrt(21/(32 pi))
+    const float c3d = 0.3731763325901154f;  // sqrt(7/(16 pi))
+    const float c3e = 1.445305721320277f;   // sqrt(105/(16 pi))
+    float z2 = z * z;
+    float Y[7] = {c3a * y * (3.f * x * x - y * y), c3b * x * y * z, c3c * y * (5.f * z2 - 1.f),
+                  c3d * z * (5.f * z2 - 3.f), c3c * x * (5.f * z2 - 1.f), c3e * z * (x * x - y * y),
+                  c3a * x * (x * x - 3.f * y * y)};
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (9 + k) + ch], rgb[ch]);
+  }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
+}
+
+// Cooperative copy of `count` consecutive attributes starting at element `first` of `src`
+// into float32 shared memory, 16-byte vector loads where aligned.  dst element e goes to
+// dst[(e / row) * (row + pad) + e % row] (pad breaks shared-memory bank conflicts).
+__device__ void stage_attr(float *dst, const void *src, int64_t first, int count, int dtype,
+                           int row, int pad) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto put = [&](int e, float v) { dst[(e / row) * (row + pad) + e % row] = v; };
+  if (dtype == RAYGS_F32) {
+    const float *s = reinterpret_cast<const float *>(src) + first;
+    int nvec = ((reinterpret_cast<uintptr_t>(s) & 15) == 0) ? count / 4 : 0;
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+    for (int i = tid; i < nvec; i += nt) {
+      float4 v = __ldg(s4 + i);
+      put(4 * i, v.x); put(4 * i + 1, v.y); put(4 * i + 2, v.z); put(4 * i + 3, v.w);
+    }
+    for (int e = 4 * nvec + tid; e < count; e += nt) put(e, __ldg(s + e));
+  } else {
+    const uint16_t *s = reinterpret_cast<const uint16_t *>(src) + first;
+    int nvec = ((reinterpret_cast<uintptr_t>(s) & 15) == 0) ? count / 8 : 0;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(s);
+    auto cvt = [&](uint16_t b) -> float {
+      if (dtype == RAYGS_F16) return __half2float(__ushort_as_half(b));
+      return __uint_as_float(uint32_t(b) << 16);
+    };
+    for (int i = tid; i < nvec; i += nt) {
+      uint4 v = __ldg(s4 + i);
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        put(8 * i + 2 * j, cvt(uint16_t(w[j] & 0xFFFF)));
+        put(8 * i + 2 * j + 1, cvt(uint16_t(w[j] >> 16)));
+      }
+    }
+    for (int e = 8 * nvec + tid; e < count; e += nt) put(e, cvt(__ldg(s + e)));
+  }
+}
+
+__device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, const DevCam &cam,
+                                             const df muc[3], const StageOut &so, const float rgb[3],
+                                             float z) {
+  df X = df_div(muc[0], muc[2]);
+  df Yv = df_div(muc[1], muc[2]);
+  df u = df_add(df_mul_f(X, cam.fx), df{cam.cx, 0.f});
+  df v = df_add(df_mul_f(Yv, cam.fy), df{cam.cy, 0.f});
+  Rec r;
+  r.a = make_float4(u.hi, v.hi, u.lo, v.lo);
+  r.b = make_float4(so.G[0], so.G[1], so.G[2], so.G[3]);
+  r.c = make_float4(so.h[0], so.h[1], so.kp, so.c2h);
+  r.d = make_float4(so.lo2o, rgb[0], rgb[1], rgb[2]);
+  P.rec[idx] = r;
+  P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
+                           uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
+  P.depth_key[idx] = __float_as_uint(z);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) {
+  constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
+  constexpr int SHP = K3 + 1;  // padded row
+  __shared__ float s_means[kPrepThreads * 3];
+  __shared__ float s_ls[kPrepThreads * 3];
+  __shared__ float s_q[kPrepThreads * 4];
+  __shared__ float s_logit[kPrepThreads];
+  __shared__ float s_sh[kPrepThreads * SHP];
+  extern __shared__ DevCam s_cams[];
+
+  const int g0 = blockIdx.x * kPrepThreads;
+  const int nb = min(kPrepThreads, P.n - g0);
+  for (int i = threadIdx.x; i < P.n_views * (int)(sizeof(DevCam) / 4); i += blockDim.x)
+    reinterpret_cast<float *>(s_cams)[i] = reinterpret_cast<const float *>(P.cams)[i];
+  stage_attr(s_means, P.means, int64_t(g0) * 3, nb * 3, RAYGS_F32, 3, 0);
+  stage_attr(s_ls, P.log_scales, int64_t(g0) * 3, nb * 3, P.scale_dtype, 3, 0);
+  stage_attr(s_q, P.quats, int64_t(g0) * 4, nb * 4, RAYGS_F32, 4, 0);
+  stage_attr(s_logit, P.logits, g0, nb, P.opacity_dtype, 1, 0);
+  stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, 1);
+  __syncthreads();
+
+  const int t = threadIdx.x;
+  if (t >= nb) return;
+  const int g = g0 + t;
+  const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
+  const float l0 = s_ls[3 * t], l1 = s_ls[3 * t + 1], l2 = s_ls[3 * t + 2];
+  const float qw = s_q[4 * t], qx = s_q[4 * t + 1], qy = s_q[4 * t + 2], qz = s_q[4 * t + 3];
+  const float logit = s_logit[t];
+  const float *coef = s_sh + t * SHP;
+
+  bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(l0) && isfinite(l1) &&
+                isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
+                isfinite(logit) && (qw * qw + qx * qx + qy * qy + qz * qz > 0.f);
+  bool degenerate = false;
+  if (finite && P.fp64_degenerate) {
+    float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
+    degenerate = (lmax - lmin) > logf(P.degenerate_ratio);
+  }
+  if (!finite) atomicAdd(&P.counters->n_nonfinite, 1ull);
+  if (degenerate) {
+    uint32_t slot = atomicAdd(P.deg_count, 1u);
+    P.deg_list[slot] = uint32_t(g);
+  }
+  if (!finite || degenerate) {
+    if (!finite)
+      for (int v = 0; v < P.n_views; ++v) P.depth_key[int64_t(v) * P.n + g] = kCulled;
+    return;
+  }
+  float Rp[9];
+  quat_rot<float>(qw, qx, qy, qz, Rp);
+  const float s[3] = {expf(l0), expf(l1), expf(l2)};
+  const float o = 1.f / (1.f + expf(-logit));
+
+  for (int v = 0; v < P.n_views; ++v) {
+    const DevCam &cam = s_cams[v];
+    const int64_t idx = int64_t(v) * P.n + g;
+    float z = depth_f32(cam, mx, my, mz);
+    if (!(z > cam.near_z)) { P.depth_key[idx] = kCulled; continue; }
+    df muc[3];
+    mean_cam_df(cam, mx, my, mz, muc);
+    const float mu[3] = {muc[0].hi, muc[1].hi, muc[2].hi};
+    StageOut so;
+    if (!view_stage<float>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+      P.depth_key[idx] = kCulled;
+      continue;
+    }
+    float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
+    float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float rgb[3];
+    sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
+    write_record(P, idx, cam, muc, so, rgb, z);
+  }
+}
+
+// FP64 vertex stage for the primitives listed by preprocess_kernel (scale ratio above
+// degenerate_ratio).  Grid-stride over the device-side list.
+template <int DEG>
+__global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const uint32_t count = *P.deg_count;
+  for (uint32_t li = blockIdx.x * blockDim.x + threadIdx.x; li < count; li += gridDim.x * blockDim.x) {
+    const int g = int(P.deg_list[li]);
+    const float mx = P.means[3 * int64_t(g)], my = P.means[3 * int64_t(g) + 1], mz = P.means[3 * int64_t(g) + 2];
+    double ls[3], qd[4];
+    for (int k = 0; k < 3; ++k) ls[k] = load_attr(P.log_scales, 3 * int64_t(g) + k, P.scale_dtype);
+    for (int k = 0; k < 4; ++k) qd[k] = P.quats[4 * int64_t(g) + k];
+    const double logit = load_attr(P.logits, g, P.opacity_dtype);
+    float coef[3 * K];
+    for (int k = 0; k < 3 * K; ++k) coef[k] = load_attr(P.sh, int64_t(g) * 3 * K + k, P.sh_dtype);
+    double Rp[9];
+    quat_rot<double>(qd[0], qd[1], qd[2], qd[3], Rp);
+    const double s[3] = {exp(ls[0]), exp(ls[1]), exp(ls[2])};
+    const double o = 1.0 / (1.0 + exp(-logit));
+    for (int v = 0; v < P.n_views; ++v) {
+      const DevCam &cam = P.cams[v];
+      const int64_t idx = int64_t(v) * P.n + g;
+      float z = depth_f32(cam, mx, my, mz);
+      if (!(z > cam.near_z)) { P.depth_key[idx] = kCulled; continue; }
+      df muc[3];
+      mean_cam_df(cam, mx, my, mz, muc);
+      const double mu[3] = {double(muc[0].hi) + double(muc[0].lo), double(muc[1].hi) + double(muc[1].lo),
+                            double(muc[2].hi) + double(muc[2].lo)};
+      StageOut so;
+      if (!view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+        P.depth_key[idx] = kCulled;
+        continue;
+      }
+      float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
+      float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+      float rgb[3];
+      sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
+      write_record(P, idx, cam, muc, so, rgb, z);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ launcher
+cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st) {
+  if (P.n == 0) return cudaSuccess;
+  int blocks = (P.n + kPrepThreads - 1) / kPrepThreads;
+  size_t dyn = sizeof(DevCam) * P.n_views;
+  cudaMemsetAsync(P.deg_count, 0, sizeof(uint32_t), st);
+  switch (P.sh_degree) {
+    case 0: preprocess_kernel<0><<<blocks, kPrepThreads, dyn, st>>>(P); break;
+    case 1: preprocess_kernel<1><<<blocks, kPrepThreads, dyn, st>>>(P); break;
+    case 2: preprocess_kernel<2><<<blocks, kPrepThreads, dyn, st>>>(P); break;
+    default: preprocess_kernel<3><<<blocks, kPrepThreads, dyn, st>>>(P); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (P.fp64_degenerate) {
+    int gb = num_sms * 4;
+    switch (P.sh_degree) {
+      case 0: preprocess_fp64_kernel<0><<<gb, 128, 0, st>>>(P); break;
+      case 1: preprocess_fp64_kernel<1><<<gb, 128, 0, st>>>(P); break;
+      case 2: preprocess_fp64_kernel<2><<<gb, 128, 0, st>>>(P); break;
+      default: preprocess_fp64_kernel<3><<<gb, 128, 0, st>>>(P); break;
+    }
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace raygs

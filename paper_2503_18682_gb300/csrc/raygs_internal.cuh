@@ -1,0 +1,215 @@
+// Internal declarations shared by the CUDA translation units of the RayGS library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "raygs.h"
+
+namespace raygs {
+
+constexpr uint32_t kCulled = 0xFFFFFFFFu;  // depth-key marker of a culled (primitive, view)
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-view constants as the kernels see them (device copy built by the plan).
+struct DevCam {
+  float fx, fy, cx, cy;
+  float ifx, ify;              // 1/fx, 1/fy
+  int W, H;
+  float R[9];                  // world -> camera, row-major
+  float t[3];
+  float near_z;
+  int mip;
+  float C[3];                  // camera centre in the world frame
+  float xmin, xmax, ymin, ymax;  // slopes of the outermost pixel-centre rays
+  int tiles_x, tiles_y;
+  int tile_base;               // first global tile id of the view
+  int pad0;
+  long long pix_base;          // first output pixel of the view
+};
+
+// 64-byte per-(primitive, view) pixel record consumed by the rasteriser.
+//   a = (u_hi, v_hi, u_lo, v_lo)   projected centre in pixels, double-float
+//   b = (G00, G01, G10, G11)       y01 = G (px - u), scaled so that y2(centre) = 1
+//   c = (h0, h1, kp, c2h)          y2 = 1 + h . (px - u); kp = (c^2-kappa)/kappa;
+//                                  c2h = c^2 log2(e) / 2
+//   d = (lo2o, r, g, b)            log2 of the (modulated) opacity; colour
+struct __align__(16) Rec {
+  float4 a, b, c, d;
+};
+
+// Device-side counters (one per plan).
+struct Counters {
+  uint32_t n_visible;       // valid (primitive, view) pairs after culling
+  uint32_t n_inst_clamped;  // min(instances, capacity)
+  unsigned long long n_instances;
+  unsigned long long n_nonfinite;
+  uint32_t overflow;
+  uint32_t pad[3];
+};
+
+struct RasterCfg {
+  float t_stop;
+  float alpha_max;
+};
+
+// Packed inclusive tile rectangle: x = tx0 | ty0 << 16, y = tx1 | ty1 << 16.
+__host__ __device__ inline uint32_t rect_count(uint2 r) {
+  uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF, ty1 = r.y >> 16;
+  return (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+}
+
+// ---------------------------------------------------------------- double-float helpers
+// Error-free transforms (Knuth two-sum, FMA two-product) written with explicitly rounded
+// intrinsics so that the compiler cannot contract or reassociate them.
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // requires |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  float e = __fmaf_rn(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, e);
+}
+
+// a / b for double-float a, b (one Newton correction; ~44 significant bits).
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  // r = a - q1 * b
+  df p = two_prod(q1, b.hi);
+  float r = __fsub_rn(a.hi, p.hi);
+  r = __fsub_rn(r, p.lo);
+  r = __fadd_rn(r, a.lo);
+  r = __fsub_rn(r, __fmul_rn(q1, b.lo));
+  float q2 = __fdiv_rn(r, b.hi);
+  return quick_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------- attribute loads
+__device__ __forceinline__ float load_attr(const void *base, int64_t idx, int dtype) {
+  if (dtype == RAYGS_F16) return __half2float(reinterpret_cast<const __half *>(base)[idx]);
+  if (dtype == RAYGS_BF16)
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
+  return reinterpret_cast<const float *>(base)[idx];
+}
+
+inline int dtype_bytes(int dtype) { return dtype == RAYGS_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------- kernel parameters
+struct PrepParams {
+  const float *means;
+  const void *log_scales;
+  const float *quats;
+  const void *logits;
+  const void *sh;
+  int sh_degree, scale_dtype, opacity_dtype, sh_dtype;
+  int n;
+  int n_views;
+  const DevCam *cams;
+  float p_min, mip_sigma2, degenerate_ratio;
+  int fp64_degenerate;
+  int tile_w, tile_h;
+  uint32_t *depth_key;
+  uint2 *rect;
+  Rec *rec;
+  Counters *counters;
+  uint32_t *deg_list;   // ids of primitives left to the FP64 kernel
+  uint32_t *deg_count;
+};
+
+struct SortPass {
+  const uint32_t *keys_in;
+  const uint32_t *vals_in;
+  uint32_t *keys_out;
+  uint32_t *vals_out;
+  const uint32_t *d_count;  // device item count (nullable: count_max is used)
+  uint32_t count_max;
+  int shift;
+  int filter;               // drop kCulled keys; value = item index
+  uint32_t *hist;           // [256][G]
+  int G;
+  uint32_t *d_total;        // receives the number of items kept (nullable)
+};
+
+struct ScanParams {
+  const uint32_t *pairs;    // sorted pair ids
+  const uint2 *rect;        // per pair
+  uint32_t *cnt;            // per sorted position
+  uint32_t *off;            // per sorted position (exclusive scan)
+  uint32_t *partial;        // [G]
+  uint32_t *tile_start;     // first sorted position of each emit tile
+  Counters *counters;
+  uint32_t capacity;
+  uint32_t tile_start_len;  // entries of tile_start
+};
+
+struct EmitParams {
+  const uint32_t *pairs;
+  const uint2 *rect;
+  const uint32_t *off;
+  const uint32_t *tile_start;
+  const DevCam *cams;
+  const Counters *counters;
+  int n;                    // primitives per view
+  uint32_t *keys;           // [capacity] global tile id
+  uint32_t *vals;           // [capacity] sorted pair position
+};
+
+struct RenderParams {
+  const DevCam *cams;
+  int n_views;
+  const uint2 *ranges;
+  const uint32_t *inst_vals;
+  const uint32_t *pairs;
+  const Rec *rec;
+  float t_stop, alpha_max;
+  float *rgb;
+  float *Tf;
+  int *ncontrib;
+  unsigned long long *eval_counts;  // [2]: evaluated and composited (pixel, primitive) pairs
+};
+
+constexpr int kEmitTile = 2048;
+
+cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st);
+cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
+cudaError_t launch_count_scan(const ScanParams &S, int G, cudaStream_t st);
+cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st);
+cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
+                          cudaStream_t st);
+
+}  // namespace raygs

@@ -1,0 +1,341 @@
+"""Thin Python binding of the RayGS C ABI (include/raygs.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library
+(``libraygs.so``, built in-tree by ``build.py``).  PyTorch supplies device memory and the
+current stream.  The functions named ``raygs_*`` mirror the C entry points one to one;
+``Renderer`` strings them together (plan sizing, workspace allocation, capacity retry).
+There is no fallback: if the library is missing every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libraygs.so")
+
+F32, F16, BF16 = 0, 1, 2
+MAX_VIEWS = 64
+
+
+class RayGSError(RuntimeError):
+    pass
+
+
+class Camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("R", C.c_float * 9),
+                ("t", C.c_float * 3), ("near_z", C.c_float), ("mip", C.c_int32)]
+
+
+class Config(C.Structure):
+    _fields_ = [("p_min", C.c_float), ("t_stop", C.c_float), ("alpha_max", C.c_float),
+                ("mip_sigma2", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("fp64_degenerate", C.c_int32), ("degenerate_ratio", C.c_float)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("means", C.c_void_p), ("log_scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("sh", C.c_void_p),
+                ("sh_degree", C.c_int32), ("scale_dtype", C.c_int32),
+                ("opacity_dtype", C.c_int32), ("sh_dtype", C.c_int32)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("n_visible", C.c_int64), ("n_instances", C.c_int64), ("capacity", C.c_int64),
+                ("n_nonfinite", C.c_int64), ("overflow", C.c_int32)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("d_means", C.c_void_p), ("d_log_scales", C.c_void_p), ("d_quats", C.c_void_p),
+                ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("raygs_config_default", None, [C.POINTER(Config)]),
+    ("raygs_status_string", C.c_char_p, [C.c_int]),
+    ("raygs_last_cuda_error", C.c_int, []),
+    ("raygs_plan_create", C.c_int, [C.POINTER(Camera), C.c_int32, C.c_int64, C.c_int64,
+                                    C.POINTER(Config), C.POINTER(C.c_void_p)]),
+    ("raygs_plan_destroy", None, [C.c_void_p]),
+    ("raygs_plan_workspace_bytes", C.c_size_t, [C.c_void_p]),
+    ("raygs_plan_bind", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("raygs_plan_set_poses", C.c_int, [C.c_void_p, C.POINTER(Camera), C.c_void_p]),
+    ("raygs_plan_num_pixels", C.c_int64, [C.c_void_p]),
+    ("raygs_plan_pixel_offset", C.c_int64, [C.c_void_p, C.c_int32]),
+    ("raygs_plan_num_tiles", C.c_int64, [C.c_void_p]),
+    ("raygs_preprocess", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p]),
+    ("raygs_bin_sort", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("raygs_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("raygs_render_backward", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.POINTER(Grads), C.c_void_p]),
+    ("raygs_read_counters", C.c_int, [C.c_void_p, C.POINTER(Counters), C.c_void_p]),
+    ("raygs_graph_capture", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
+    ("raygs_graph_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+]
+_DEBUG_SIGS = [
+    ("raygs_debug_render_counted", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.POINTER(C.c_ulonglong), C.c_void_p]),
+    ("raygs_debug_buffer", C.c_void_p, [C.c_void_p, C.c_int]),
+]
+
+
+def lib():
+    """Load libraygs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RayGSError(f"RayGS CUDA library not built ({LIB_PATH}); run "
+                             "`python -m paper_2503_18682_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in _SIGS + _DEBUG_SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = lib().raygs_status_string(status).decode()
+        extra = f" (cudaError {lib().raygs_last_cuda_error()})" if status == 3 else ""
+        raise RayGSError(f"{what}: {msg}{extra}")
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_cameras(cams) -> C.Array:
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        a = arr[i]
+        a.fx, a.fy, a.cx, a.cy = float(c["fx"]), float(c["fy"]), float(c["cx"]), float(c["cy"])
+        a.width, a.height = int(c["width"]), int(c["height"])
+        R = np.asarray(c["R"], dtype=np.float32).reshape(9)
+        t = np.asarray(c["t"], dtype=np.float32).reshape(3)
+        for k in range(9):
+            a.R[k] = float(R[k])
+        for k in range(3):
+            a.t[k] = float(t[k])
+        a.near_z = float(c.get("near", 0.01))
+        a.mip = 1 if c.get("mip", False) else 0
+    return arr
+
+
+def make_config(**kw) -> Config:
+    cfg = Config()
+    lib().raygs_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+_DT = {"f32": F32, "f16": F16, "bf16": BF16}
+
+
+def scene_to_device(scene: dict, device="cuda") -> dict:
+    """numpy scene (scenes.py layout) -> dict of contiguous torch tensors on `device`."""
+    torch = _torch()
+    out = {"sh_degree": int(scene["sh_degree"])}
+    for key, tag in (("means", None), ("log_scales", "scale_dtype"), ("quats", None),
+                     ("opacity_logits", "opacity_dtype"), ("sh", "sh_dtype")):
+        a = np.ascontiguousarray(scene[key])
+        dt = scene.get(tag, "f32") if tag else "f32"
+        if dt == "bf16":
+            t = torch.from_numpy(a.view(np.int16)).view(torch.bfloat16)
+        elif dt == "f16":
+            t = torch.from_numpy(a.astype(np.float16))
+        else:
+            t = torch.from_numpy(a.astype(np.float32))
+        out[key] = t.to(device).contiguous()
+    return out
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    return {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[t.dtype]
+
+
+def make_scene(st: dict) -> Scene:
+    s = Scene()
+    s.n = int(st["means"].shape[0])
+    s.means = st["means"].data_ptr()
+    s.log_scales = st["log_scales"].data_ptr()
+    s.quats = st["quats"].data_ptr()
+    s.opacity_logits = st["opacity_logits"].data_ptr()
+    s.sh = st["sh"].data_ptr()
+    s.sh_degree = int(st["sh_degree"])
+    s.scale_dtype = _dtype_code(st["log_scales"])
+    s.opacity_dtype = _dtype_code(st["opacity_logits"])
+    s.sh_dtype = _dtype_code(st["sh"])
+    return s
+
+
+# ------------------------------------------------------------------ C entry points
+
+def raygs_plan_create(cams, n_gaussians: int, max_instances: int, cfg: Config | None = None):
+    arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    h = C.c_void_p()
+    _check(lib().raygs_plan_create(arr, len(arr), int(n_gaussians), int(max_instances),
+                                   C.byref(cfg) if cfg is not None else None, C.byref(h)),
+           "raygs_plan_create")
+    return h
+
+
+def raygs_plan_destroy(plan):
+    lib().raygs_plan_destroy(plan)
+
+
+def raygs_plan_workspace_bytes(plan) -> int:
+    return int(lib().raygs_plan_workspace_bytes(plan))
+
+
+def raygs_plan_bind(plan, ptr: int, nbytes: int):
+    _check(lib().raygs_plan_bind(plan, C.c_void_p(ptr), nbytes), "raygs_plan_bind")
+
+
+def raygs_plan_set_poses(plan, cams, stream=None):
+    arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    _check(lib().raygs_plan_set_poses(plan, arr, stream_ptr(stream)), "raygs_plan_set_poses")
+
+
+def raygs_preprocess(plan, scene: Scene, stream=None):
+    _check(lib().raygs_preprocess(plan, C.byref(scene), stream_ptr(stream)), "raygs_preprocess")
+
+
+def raygs_bin_sort(plan, stream=None):
+    _check(lib().raygs_bin_sort(plan, stream_ptr(stream)), "raygs_bin_sort")
+
+
+def raygs_render(plan, rgb, T_final=None, n_contrib=None, stream=None):
+    _check(lib().raygs_render(plan, rgb.data_ptr(), T_final.data_ptr() if T_final is not None else None,
+                              n_contrib.data_ptr() if n_contrib is not None else None,
+                              stream_ptr(stream)), "raygs_render")
+
+
+def raygs_render_backward(plan, scene: Scene, T_final, n_contrib, dL_drgb, dL_dT, grads: Grads,
+                          stream=None):
+    _check(lib().raygs_render_backward(plan, C.byref(scene), T_final.data_ptr(), n_contrib.data_ptr(),
+                                       dL_drgb.data_ptr(), dL_dT.data_ptr() if dL_dT is not None else None,
+                                       C.byref(grads), stream_ptr(stream)), "raygs_render_backward")
+
+
+def raygs_read_counters(plan, stream=None) -> dict:
+    c = Counters()
+    _check(lib().raygs_read_counters(plan, C.byref(c), stream_ptr(stream)), "raygs_read_counters")
+    return dict(n_visible=c.n_visible, n_instances=c.n_instances, capacity=c.capacity,
+                n_nonfinite=c.n_nonfinite, overflow=c.overflow)
+
+
+def raygs_graph_capture(plan, scene: Scene, rgb, T_final=None, n_contrib=None, stream=None):
+    _check(lib().raygs_graph_capture(plan, C.byref(scene), rgb.data_ptr(),
+                                     T_final.data_ptr() if T_final is not None else None,
+                                     n_contrib.data_ptr() if n_contrib is not None else None,
+                                     stream_ptr(stream)), "raygs_graph_capture")
+
+
+def raygs_graph_launch(plan, stream=None):
+    _check(lib().raygs_graph_launch(plan, stream_ptr(stream)), "raygs_graph_launch")
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Renderer:
+    """A plan + its device workspace for a fixed camera set and primitive count."""
+
+    def __init__(self, cams, n_gaussians: int, capacity: int | None = None, device="cuda", **cfg):
+        torch = _torch()
+        self.cams = list(cams)
+        self.n = int(n_gaussians)
+        self.device = torch.device(device)
+        self.cfg = make_config(**cfg)
+        if capacity is None:
+            capacity = max(1 << 16, 4 * self.n * len(self.cams))
+        self.capacity = int(min(capacity, (1 << 32) - 4096))
+        self.plan = None
+        self._ws = None
+        self._make_plan()
+
+    def _make_plan(self):
+        torch = _torch()
+        if self.plan is not None:
+            raygs_plan_destroy(self.plan)
+        self.plan = raygs_plan_create(self.cams, self.n, self.capacity, self.cfg)
+        nb = raygs_plan_workspace_bytes(self.plan)
+        self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        raygs_plan_bind(self.plan, self._ws.data_ptr(), nb)
+        self.num_pixels = int(lib().raygs_plan_num_pixels(self.plan))
+        self.num_tiles = int(lib().raygs_plan_num_tiles(self.plan))
+        self.pixel_offsets = [int(lib().raygs_plan_pixel_offset(self.plan, v))
+                              for v in range(len(self.cams))]
+
+    def __del__(self):
+        try:
+            if self.plan is not None:
+                raygs_plan_destroy(self.plan)
+        except Exception:
+            pass
+
+    def alloc_outputs(self):
+        torch = _torch()
+        rgb = torch.empty((self.num_pixels, 3), dtype=torch.float32, device=self.device)
+        T = torch.empty(self.num_pixels, dtype=torch.float32, device=self.device)
+        nc = torch.empty(self.num_pixels, dtype=torch.int32, device=self.device)
+        return rgb, T, nc
+
+    def forward(self, scene_t: dict, rgb=None, T=None, nc=None, stream=None, check=True):
+        """preprocess + bin_sort + render.  With check=True the counters are read (one
+        sync) and the plan is regrown and the call repeated if the instance capacity
+        overflowed."""
+        if rgb is None:
+            rgb, T, nc = self.alloc_outputs()
+        sc = make_scene(scene_t)
+        for _attempt in range(3):
+            raygs_preprocess(self.plan, sc, stream)
+            raygs_bin_sort(self.plan, stream)
+            raygs_render(self.plan, rgb, T, nc, stream)
+            if not check:
+                break
+            ctr = raygs_read_counters(self.plan, stream)
+            self.last_counters = ctr
+            if not ctr["overflow"]:
+                break
+            self.capacity = int(min(ctr["n_instances"] * 1.15 + 4096, (1 << 32) - 4096))
+            self._make_plan()
+        return rgb, T, nc
+
+    def view_image(self, rgb, v: int):
+        c = self.cams[v]
+        o = self.pixel_offsets[v]
+        return rgb[o:o + c["width"] * c["height"]].view(c["height"], c["width"], -1)
+
+    def counted_render(self, rgb, T=None, nc=None, stream=None):
+        """Instrumented render: returns (evaluated pairs, composited pairs)."""
+        out = (C.c_ulonglong * 2)()
+        _check(lib().raygs_debug_render_counted(self.plan, rgb.data_ptr(),
+                                                T.data_ptr() if T is not None else None,
+                                                nc.data_ptr() if nc is not None else None,
+                                                out, stream_ptr(stream)), "raygs_debug_render_counted")
+        return int(out[0]), int(out[1])
+
+    def debug_buffer(self, which: int) -> int:
+        return int(lib().raygs_debug_buffer(self.plan, which) or 0)
