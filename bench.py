@@ -1,0 +1,347 @@
+"""Benchmark of the RayGS hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole hot path (per-primitive vertex stage, depth + tile binning,
+tile rasterisation) over the stereo-VR batch: 3M blob primitives (10% near-flat, scale ratio
+> 1e3) seen by 16 views of uneven size (4 stereo pairs at 2064x2208 per eye plus 8 views of
+random size in [640,1920]x[480,1080]), launched as one captured CUDA graph.  The metric is
+stereo frames/s in its strict reading: complete 16-view batches per second (each batch
+holds 4 stereo pairs).  Inputs (708 MB of attributes, 3 GB of per-view records) are larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded pixel sample of the same workload instead (the only other place that runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stereo frames/s + Gaussian-pixel evals/s at 3M Gaussians; fwd+bwd ms/view at 1.5M"
+UNIT = "stereo frames/s (16-view batches/s)"
+WORKLOAD = ("stereo-VR batch: 3M blob primitives (10% axis ratio > 1e3), 16 views "
+            "(4 stereo pairs 2064x2208 per eye + 8 random 640-1920 x 480-1080), one CUDA graph")
+
+# algorithmic FP32 flops of the rasteriser (FMA = 2): per evaluated (pixel, primitive) pair
+# and extra per composited pair; see the design notes
+FLOP_EVAL = 17
+FLOP_COMP = 15
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------- reference arm
+
+def cpu_oracle_sample(scene, cams, n_pixels=96, seed=11, threads=0):
+    """Time the FP64 oracle on a bounded sample: per view, the per-primitive setup (one call
+    with a single pixel) plus `n_pixels` sampled pixels of view 0; extrapolate to seconds per
+    16-view batch.  Returns (seconds_per_batch, cores, description)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    idx = rng.choice(W * H, n_pixels, replace=False)
+    pix = np.stack([idx % W, idx // W], axis=1).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, pixels=pix[:1], threads=threads)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, pixels=pix, threads=threads)
+    t_all = time.perf_counter() - t0
+    t_pix = max(t_all - t_setup, 1e-9) / n_pixels
+    P = sum(c["width"] * c["height"] for c in cams)
+    per_batch = len(cams) * t_setup + P * t_pix
+    desc = (f"FP64 oracle, {n_pixels} sampled pixels of view 0 against all {scene['means'].shape[0]} "
+            f"primitives plus one per-view setup; extrapolated to {len(cams)} views / {P} pixels")
+    return per_batch, cores, desc, t_setup + t_all
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2503_18682_gb300 import scenes
+    scene, cams = scenes.workload_stereo_batch()
+    times = []
+    cores = 1
+    desc = ""
+    for _ in range(args.warmup):
+        cpu_oracle_sample(scene, cams, n_pixels=8)
+    for _ in range(args.steps):
+        per_batch, cores, desc, wall = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
+        times.append(per_batch)
+    spb = statistics.median(times)
+    value = 1.0 / spb
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=spb * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, n_gaussians=int(scene["means"].shape[0]), views=len(cams)),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=desc),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2503_18682_gb300 import build, raygs, scenes
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = peaks()
+
+    scene, cams = scenes.workload_stereo_batch(n=args.n)
+    n = int(scene["means"].shape[0])
+    st = raygs.scene_to_device(scene, dev)
+    r = raygs.Renderer(cams, n, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream())
+    rgb, T, nc = r.alloc_outputs()
+    with torch.cuda.stream(stream):
+        r.forward(st, rgb, T, nc, stream=stream)            # sizes the instance capacity
+        ctr = dict(r.last_counters)
+        # headroom for pose changes, then a fresh plan at the final capacity
+        r.capacity = int(min(ctr["n_instances"] * 1.10 + 65536, (1 << 32) - 4096))
+        r._make_plan()
+        sc = raygs.make_scene(st)
+        r.forward(st, rgb, T, nc, stream=stream)
+        ctr = dict(r.last_counters)
+        evals, comps = r.counted_render(rgb, T, nc, stream=stream)
+        raygs.raygs_graph_capture(r.plan, sc, rgb, T, nc, stream)
+    stream.synchronize()
+
+    def timed(fn, k):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(k):
+                fn()
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    # per-stage breakdown (untimed w.r.t. the headline): events on the launching stream
+    def stage_times(k=5):
+        out = {}
+        with torch.cuda.stream(stream):
+            raygs.raygs_preprocess(r.plan, sc, stream)
+            raygs.raygs_bin_sort(r.plan, stream)
+        out["preprocess_ms"] = timed(lambda: raygs.raygs_preprocess(r.plan, sc, stream), k)
+        out["bin_sort_ms"] = timed(lambda: raygs.raygs_bin_sort(r.plan, stream), k)
+        out["render_ms"] = timed(lambda: raygs.raygs_render(r.plan, rgb, T, nc, stream), k)
+        return out
+
+    stages = stage_times()
+
+    # headline: W warm-up graph launches, K timed, barrier + sync on both sides
+    for _ in range(args.warmup):
+        raygs.raygs_graph_launch(r.plan, stream)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            raygs.raygs_graph_launch(r.plan, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    clocks = clk.summary()
+    batches = args.steps * world
+    value = batches / (ms_max * args.steps / 1e3)
+
+    # e2e through the C ABI with host buffers: pinned H2D of the attributes, graph, D2H image
+    host = {k: v.to("cpu").pin_memory() for k, v in st.items() if hasattr(v, "to")}
+    rgb_host = torch.empty(rgb.shape, dtype=rgb.dtype, pin_memory=True)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = rgb.numel() * rgb.element_size()
+
+    def e2e_step():
+        for k, v in host.items():
+            st[k].copy_(v, non_blocking=True)
+        raygs.raygs_graph_launch(r.plan, stream)
+        rgb_host.copy_(rgb, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            e2e_step()
+    stream.synchronize()
+    e2e_ms = max_over_ranks(timed(e2e_step, max(2, min(args.steps, 10))), world)
+
+    # roofline of the dominant kernel (the rasteriser: plain FP32 ALU work)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    flops = FLOP_EVAL * evals + FLOP_COMP * comps
+    peak_tf = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    ach_tf = flops / (stages["render_ms"] * 1e-3) / 1e12
+    # HBM view of the vertex stage: attributes read once, per visible pair 64+8+4 B written,
+    # plus the 4 B key of every (primitive, view)
+    attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
+    prep_bytes = attr_bytes + 4 * n * len(cams) + 76 * ctr["n_visible"]
+    gpu_launches = args.steps * (2 + 3 * 4 + 3 + 1 + 3 * ((max(1, (r.num_tiles - 1).bit_length()) + 7) // 8) + 1 + 1)
+
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms_max, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config=dict(workload=WORKLOAD, n_gaussians=n, views=len(cams), pixels=r.num_pixels,
+                    tiles=r.num_tiles, tile=f"{r.cfg.tile_w}x{r.cfg.tile_h}",
+                    l2="inputs larger than L2 (no flush)", parallelism=f"replica x{world}"),
+        stereo_pairs_per_s=4 * value,
+        gaussian_pixel_evals_per_s=evals / (stages["render_ms"] * 1e-3),
+        composited_pairs_per_s=comps / (stages["render_ms"] * 1e-3),
+        evaluated_pairs=evals, composited_pairs=comps,
+        n_visible=ctr["n_visible"], n_instances=ctr["n_instances"],
+        stages=dict(stages, preprocess_hbm_gbs=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9,
+                    preprocess_hbm_frac=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"]),
+        roofline=dict(bound="alu", kernel="render_kernel<16,16>", achieved=ach_tf, peak=peak_tf,
+                      unit="TFLOP/s", frac=ach_tf / peak_tf, traffic=None,
+                      peak_note=f"FP32 {sms} SMs x 128 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz (derived)",
+                      algorithmic=f"{FLOP_EVAL} flop per evaluated pair + {FLOP_COMP} per composited pair"),
+        clocks=clocks,
+        e2e=dict(value=1e3 / e2e_ms, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
+        gpu_launches=int(gpu_launches),
+    )
+    if rank == 0 and not args.no_cpu_baseline:
+        spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
+        line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=3_000_000)
+    ap.add_argument("--ref-pixels", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
