@@ -211,6 +211,40 @@ raygs_status raygs_graph_capture(raygs_plan *plan, const raygs_scene *scene, flo
 /* Launch the captured graph on `stream`. */
 raygs_status raygs_graph_launch(raygs_plan *plan, void *stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Bytes of the device array raygs_render_noalloc works in (32 MiB). */
+#define RAYGS_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/*
+ * The same forward render as raygs_preprocess + raygs_bin_sort + raygs_render, for callers
+ * that may not allocate device memory: a plugin or engine integration running inside a
+ * host application that owns the whole device heap and only hands out its own buffers, or
+ * code under a memory budget enforced by an outer allocator.  This entry point allocates
+ * nothing (no cudaMalloc/cudaFree, no host heap): all intermediate buffers live in one
+ * file-scope device array of RAYGS_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * keeps reserved until the process exits.  The paper has no counterpart; it is a
+ * deployment variant of the hot path.
+ *
+ *  - Inputs/outputs as in raygs_preprocess and raygs_render (caller-owned device buffers);
+ *    cams is a host array of n_views cameras; cfg may be NULL for the defaults.
+ *  - Size limit: the per-(primitive, view) buffers (about 100 bytes each), the tile ranges
+ *    and a sort histogram must fit in the array, and the remaining space bounds the
+ *    (primitive, tile) instances.  A problem that does not fit is rejected with
+ *    RAYGS_ERR_CAPACITY before any work is enqueued; one whose instances overflow the
+ *    remaining space returns RAYGS_ERR_CAPACITY after the render (image incomplete).
+ *  - Set-up: the first call on each device, with that device current, looks up the
+ *    array's device address (which loads the module on that device); make that first call
+ *    before any stream capture on that device.
+ *  - The call reads a device counter at the end and therefore synchronises `stream`.
+ *  - Every call shares the one array, which keeps the last call's contents (the call
+ *    clears what must start at zero).  Calls that overlap on the GPU (different streams or
+ *    host threads without ordering between them) race on it.
+ */
+raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n_views, const raygs_scene *scene,
+                                  const raygs_config *cfg, float *rgb, float *T_final,
+                                  int32_t *n_contrib, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

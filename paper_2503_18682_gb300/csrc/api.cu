@@ -10,6 +10,10 @@
 
 using namespace raygs;
 
+namespace raygs {
+void note_cuda_error(cudaError_t e);
+}
+
 namespace {
 thread_local int g_last_cuda_error = 0;
 
@@ -21,6 +25,11 @@ raygs_status cuda_fail(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
+void raygs::note_cuda_error(cudaError_t e) { g_last_cuda_error = int(e); }
+
+namespace {
 int bits_for(uint64_t n) {  // bits needed to represent values < n
   int b = 0;
   while (b < 32 && (uint64_t(1) << b) < n) ++b;

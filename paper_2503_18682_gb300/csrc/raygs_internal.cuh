@@ -204,6 +204,9 @@ struct RenderParams {
 
 constexpr int kEmitTile = 2048;
 
+// Records e as the thread's last CUDA error (read back by raygs_last_cuda_error).
+void note_cuda_error(cudaError_t e);
+
 cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st);
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
 cudaError_t launch_count_scan(const ScanParams &S, int G, cudaStream_t st);

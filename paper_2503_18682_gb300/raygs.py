@@ -78,6 +78,9 @@ _SIGS = [
     ("raygs_graph_capture", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     ("raygs_graph_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("raygs_render_noalloc", C.c_int, [C.POINTER(Camera), C.c_int32, C.POINTER(Scene),
+                                       C.POINTER(Config), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
 ]
 _DEBUG_SIGS = [
     ("raygs_debug_render_counted", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -255,6 +258,20 @@ def raygs_graph_capture(plan, scene: Scene, rgb, T_final=None, n_contrib=None, s
 
 def raygs_graph_launch(plan, stream=None):
     _check(lib().raygs_graph_launch(plan, stream_ptr(stream)), "raygs_graph_launch")
+
+
+def raygs_render_noalloc(cams, scene: Scene, cfg: Config | None, rgb, T_final=None, n_contrib=None,
+                         stream=None, check=True) -> int:
+    """Allocation-free forward render (see include/raygs.h); returns the status code and
+    raises on failure when check=True."""
+    arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    st = lib().raygs_render_noalloc(arr, len(arr), C.byref(scene), C.byref(cfg) if cfg is not None else None,
+                                    rgb.data_ptr(), T_final.data_ptr() if T_final is not None else None,
+                                    n_contrib.data_ptr() if n_contrib is not None else None,
+                                    stream_ptr(stream))
+    if check:
+        _check(st, "raygs_render_noalloc")
+    return st
 
 
 # ------------------------------------------------------------------ convenience wrapper
