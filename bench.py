@@ -199,10 +199,28 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     pk = peaks()
 
-    scene, cams = scenes.workload_stereo_batch(n=args.n)
+    if args.workload == "mip720":
+        scene, cams = scenes.workload_mip_720p()
+    else:
+        scene, cams = scenes.workload_stereo_batch(n=args.n)
     n = int(scene["means"].shape[0])
     st = raygs.scene_to_device(scene, dev)
     r = raygs.Renderer(cams, n, device=dev)
+    if args.mode == "profile":
+        # for ncu: size the plan once, then W + K direct pipeline passes, nothing else
+        stream = torch.cuda.current_stream()
+        rgb, T, nc = r.alloc_outputs()
+        r.forward(st, rgb, T, nc)
+        sc = raygs.make_scene(st)
+        for _ in range(args.warmup + args.steps):
+            raygs.raygs_preprocess(r.plan, sc)
+            raygs.raygs_bin_sort(r.plan)
+            raygs.raygs_render(r.plan, rgb, T, nc)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps(dict(mode="profile", workload=args.workload, passes=args.warmup + args.steps,
+                                  counters=r.last_counters)), flush=True)
+        return
     stream = torch.cuda.Stream(device=dev)
     stream.wait_stream(torch.cuda.current_stream())
     rgb, T, nc = r.alloc_outputs()
@@ -292,7 +310,10 @@ def run_ours(args, world, rank, local):
     # plus the 4 B key of every (primitive, view)
     attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
     prep_bytes = attr_bytes + 4 * n * len(cams) + 76 * ctr["n_visible"]
-    gpu_launches = args.steps * (2 + 3 * 4 + 3 + 1 + 3 * ((max(1, (r.num_tiles - 1).bit_length()) + 7) // 8) + 1 + 1)
+    # kernels per pass: preprocess (2), depth sort (4 x 3), rows count + scan (4), row spans
+    # (1), span scan (3), emission (1), tile sort (passes x 3), ranges (1), rasteriser (1)
+    tile_bits = max(1, (r.num_tiles - 1).bit_length())
+    gpu_launches = args.steps * (2 + 12 + 4 + 1 + 3 + 1 + 3 * ((tile_bits + 8) // 9) + 1 + 1)
 
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -332,6 +353,8 @@ def main():
     ap.add_argument("--n", type=int, default=3_000_000)
     ap.add_argument("--ref-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

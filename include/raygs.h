@@ -84,8 +84,10 @@ typedef struct {
   float alpha_max;        /* rendered opacity clamp (0.99) */
   float mip_sigma2;       /* sigma^2 of Sec. 5 in pixel^2 at unit distance (0.1) */
   int32_t tile_w, tile_h; /* screen tile in pixels: 16x16 (default), 16x8, 32x16 or 8x8 */
-  int32_t fp64_degenerate; /* 1: FP64 vertex stage for primitives whose scale ratio
-                              max/min exceeds degenerate_ratio (default 1) */
+  int32_t fp64_degenerate; /* FP64 vertex stage for near-degenerate primitives (scale
+                              ratio max/min > degenerate_ratio): 0 never; 1 (default) in
+                              the views where the float32 solve is ill-conditioned (seen
+                              nearly edge-on); 2 in every view where they are visible */
   float degenerate_ratio; /* 1e3 */
 } raygs_config;
 
@@ -228,7 +230,7 @@ raygs_status raygs_graph_launch(raygs_plan *plan, void *stream);
  *
  *  - Inputs/outputs as in raygs_preprocess and raygs_render (caller-owned device buffers);
  *    cams is a host array of n_views cameras; cfg may be NULL for the defaults.
- *  - Size limit: the per-(primitive, view) buffers (about 100 bytes each), the tile ranges
+ *  - Size limit: the per-(primitive, view) buffers (about 140 bytes each), the tile ranges
  *    and a sort histogram must fit in the array, and the remaining space bounds the
  *    (primitive, tile) instances.  A problem that does not fit is rejected with
  *    RAYGS_ERR_CAPACITY before any work is enqueued; one whose instances overflow the

@@ -4,11 +4,12 @@
 //      depth.  The first pass reads the dense per-(view, primitive) key array, drops
 //      culled entries and materialises the pair index as the value, so ties keep the
 //      primitive order within a view.
-//   2. Per sorted pair: number of covered tiles, exclusive scan -> instance offsets.
-//   3. Load-balanced emission: one thread per instance writes (global tile id, sorted
-//      position); instances come out in depth order.
-//   4. Stable LSD radix sort of the instances by tile id -> per tile, depth order.
-//   5. Per-tile [start, end) ranges.
+//   2. Two-level, load-balanced expansion in that order: each pair -> the tile rows of its
+//      screen rectangle; each row -> the tiles of the row whose pixel centres can meet the
+//      pair's support ellipse (an exact conic test, so tiles the support misses get no
+//      instance); each tile -> one instance (global tile id, sorted pair position).
+//   3. Stable LSD radix sort of the instances by tile id -> per tile, depth order.
+//   4. Per-tile [start, end) ranges.
 //
 // The radix sort is reduce-then-scan (upsweep histogram, one-CTA scan, downsweep
 // scatter) with persistent CTAs that own contiguous tile ranges: no CTA ever waits on
@@ -22,7 +23,6 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortIPT = 16;
 constexpr int kSortTile = kSortThreads * kSortIPT;  // 4096 items
-
 
 __device__ __forceinline__ void cta_tiles(uint32_t count, uint32_t &lo, uint32_t &hi) {
   uint32_t ntiles = (count + kSortTile - 1) / kSortTile;
@@ -78,8 +78,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_upsweep(SortPass p) {
   }
 }
 
-// Exclusive scan of `n` entries in place with one CTA of 1024 threads; the total is
-// written to *d_total when non-null.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -90,8 +88,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
   return x;
 }
 
-// Block-wide exclusive scan (blockDim.x multiple of 32, <= 1024). Returns the exclusive
-// prefix; *total receives the block total.  Uses `ws` (>= 32 words of shared memory).
+// Block-wide exclusive scan (blockDim.x multiple of 32, <= 1024).  Returns the exclusive
+// prefix; *total receives the block total.  Uses `ws` (>= 33 words of shared memory).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *ws, uint32_t *total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t inc = warp_incl_scan(x);
@@ -110,6 +108,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *ws, ui
   return r;
 }
 
+// Exclusive scan of `n` entries in place with one CTA of 1024 threads; the total goes to
+// *d_total when non-null.
 __global__ void __launch_bounds__(1024) scan_single_cta(uint32_t *data, int n, uint32_t *d_total) {
   __shared__ uint32_t ws[33];
   const int seg = (n + 1023) / 1024;
@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
       s_tot[d] = run;
     }
     __syncthreads();
-    // exclusive scan of the tile's digit counts
     {
       constexpr int PER = (R + kSortThreads - 1) / kSortThreads;
       uint32_t loc[PER];
@@ -224,15 +223,20 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
 }
 
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
-  sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
-  scan_single_cta<<<1, 1024, 0, st>>>(p.hist, 256 * p.G, p.d_total);
-  sort_downsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  if (p.bits == 9) {
+    sort_upsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
+    scan_single_cta<<<1, 1024, 0, st>>>(p.hist, 512 * p.G, p.d_total);
+    sort_downsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
+  } else {
+    sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+    scan_single_cta<<<1, 1024, 0, st>>>(p.hist, 256 * p.G, p.d_total);
+    sort_downsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------- tile counts and scan
-
-__device__ __forceinline__ void cta_range_items(uint32_t count, uint32_t &lo, uint32_t &hi) {
+// --------------------------------------------------------------- generic unit scan
+__device__ __forceinline__ void cta_range_units(uint32_t count, uint32_t &lo, uint32_t &hi) {
   constexpr uint32_t U = 1024;
   uint32_t nu = (count + U - 1) / U;
   uint32_t t0 = uint32_t((uint64_t(nu) * blockIdx.x) / gridDim.x);
@@ -241,47 +245,43 @@ __device__ __forceinline__ void cta_range_items(uint32_t count, uint32_t &lo, ui
   hi = min(t1 * U, count);
 }
 
-__global__ void __launch_bounds__(256) count_tiles_kernel(ScanParams S) {
+__global__ void __launch_bounds__(256) scan_reduce_kernel(ScanJob J) {
   __shared__ uint32_t ws[33];
   uint32_t lo, hi;
-  cta_range_items(S.counters->n_visible, lo, hi);
+  cta_range_units(*J.d_n, lo, hi);
   uint32_t s = 0;
-  for (uint32_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-    uint32_t c = rect_count(S.rect[S.pairs[p]]);
-    S.cnt[p] = c;
-    s += c;
-  }
+  for (uint32_t p = lo + threadIdx.x; p < hi; p += blockDim.x) s += J.cnt[p];
   uint32_t tot;
   block_excl_scan(s, ws, &tot);
-  if (threadIdx.x == 0) S.partial[blockIdx.x] = tot;
+  if (threadIdx.x == 0) J.partial[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the G <= 1024 per-CTA partial sums (64-bit running total), and the
-// instance totals: n_instances, the capacity-clamped count and the overflow flag.
-__global__ void __launch_bounds__(32) scan_partials_kernel(ScanParams S, int G) {
+// Exclusive scan of the G <= 1024 per-CTA partial sums (64-bit running total); writes the
+// total, the capacity-clamped total and the overflow flag.
+__global__ void __launch_bounds__(32) scan_partials_kernel(ScanJob J, int G) {
   if (threadIdx.x != 0) return;
   unsigned long long run = 0;
   for (int i = 0; i < G; ++i) {
-    uint32_t v = S.partial[i];
-    S.partial[i] = uint32_t(min(run, 0xFFFFFFFFull));
+    uint32_t v = J.partial[i];
+    J.partial[i] = uint32_t(min(run, 0xFFFFFFFFull));
     run += v;
   }
-  S.counters->n_instances = run;
-  S.counters->n_inst_clamped = run > S.capacity ? S.capacity : uint32_t(run);
-  S.counters->overflow = run > S.capacity ? 1u : 0u;
+  *J.d_total = run;
+  *J.d_total_clamped = run > J.cap ? J.cap : uint32_t(run);
+  if (run > J.cap) *J.d_overflow = 1u;
 }
 
-__global__ void __launch_bounds__(256) offsets_kernel(ScanParams S) {
+__global__ void __launch_bounds__(256) scan_offsets_kernel(ScanJob J) {
   __shared__ uint32_t ws[33];
   uint32_t lo, hi;
-  cta_range_items(S.counters->n_visible, lo, hi);
-  uint32_t carry = S.partial[blockIdx.x];
+  cta_range_units(*J.d_n, lo, hi);
+  uint32_t carry = J.partial[blockIdx.x];
   for (uint32_t base = lo; base < hi; base += 256 * 4) {
     uint32_t c[4], s = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint32_t p = base + threadIdx.x * 4 + j;
-      c[j] = p < hi ? S.cnt[p] : 0u;
+      c[j] = p < hi ? J.cnt[p] : 0u;
       s += c[j];
     }
     uint32_t tot;
@@ -290,11 +290,10 @@ __global__ void __launch_bounds__(256) offsets_kernel(ScanParams S) {
     for (int j = 0; j < 4; ++j) {
       uint32_t p = base + threadIdx.x * 4 + j;
       if (p < hi) {
-        S.off[p] = run;
-        // every emit tile whose first instance falls in [run, run + c) starts at p
+        J.off[p] = run;
+        // every output block whose first output falls in [run, run + c) starts at unit p
         uint32_t t = (run + kEmitTile - 1) / kEmitTile;
-        for (; uint64_t(t) * kEmitTile < uint64_t(run) + c[j] && t < S.tile_start_len; ++t)
-          S.tile_start[t] = p;
+        for (; uint64_t(t) * kEmitTile < uint64_t(run) + c[j] && t < J.tstart_len; ++t) J.tile_start[t] = p;
       }
       run += c[j];
     }
@@ -302,68 +301,184 @@ __global__ void __launch_bounds__(256) offsets_kernel(ScanParams S) {
   }
 }
 
-// ------------------------------------------------------------------- emission
+cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st) {
+  scan_reduce_kernel<<<G, 256, 0, st>>>(J);
+  scan_partials_kernel<<<1, 32, 0, st>>>(J, G);
+  scan_offsets_kernel<<<G, 256, 0, st>>>(J);
+  return cudaGetLastError();
+}
 
-__global__ void __launch_bounds__(256) emit_kernel(EmitParams E) {
+// ------------------------------------------------------------ pair -> tile rows
+__global__ void __launch_bounds__(256) count_rows_kernel(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt,
+                                                         const Counters *c) {
+  const uint32_t n = c->n_visible;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    uint2 r = rect[pairs[p]];
+    cnt[p] = (r.y >> 16) - (r.x >> 16) + 1;
+  }
+}
+
+cudaError_t launch_count_rows(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt, const Counters *c, int G,
+                              cudaStream_t st) {
+  count_rows_kernel<<<G, 256, 0, st>>>(pairs, rect, cnt, c);
+  return cudaGetLastError();
+}
+
+// Pixel-centre columns of the band ya <= y <= yb (pixel-centre rows) inside the ellipse.
+// The right boundary x_r(y) is concave with its maximum at the rightmost point of the
+// ellipse, the left one convex: clamping that point's y into the band gives the extremes.
+__device__ __forceinline__ bool ellipse_band(const Ell &e, float ya, float yb, float &xa, float &xb) {
+  const float rho = e.rho * 1.001f + 1e-6f;
+  const float hy = sqrtf(rho * e.a / e.det);
+  const float lo = fmaxf(ya - e.cy, -hy), hi = fminf(yb - e.cy, hy);
+  if (lo > hi) return false;
+  const float hx = sqrtf(rho * e.d / e.det);
+  const float ydx = -e.b * hx / e.d;  // y offset of the rightmost point
+  const float yr = fminf(fmaxf(ydx, lo), hi), yl = fminf(fmaxf(-ydx, lo), hi);
+  const float xr = (-e.b * yr + sqrtf(fmaxf(e.a * rho - e.det * yr * yr, 0.f))) / e.a;
+  const float xl = (-e.b * yl - sqrtf(fmaxf(e.a * rho - e.det * yl * yl, 0.f))) / e.a;
+  xa = e.cx + xl;
+  xb = e.cx + xr;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   __shared__ uint32_t s_off[kEmitTile + 1];
   __shared__ uint32_t s_pair[kEmitTile + 1];
-  __shared__ uint2 s_rect[kEmitTile + 1];
-  const uint32_t total = E.counters->n_inst_clamped;
-  const unsigned long long total_all = E.counters->n_instances;
-  const uint32_t nvis = E.counters->n_visible;
+  const uint32_t total = R.counters->n_rows_clamped;
+  const unsigned long long total_all = R.counters->n_rows;
+  const uint32_t nvis = R.counters->n_visible;
   const uint32_t ntile = (total + kEmitTile - 1) / kEmitTile;
   const unsigned long long ntile_all = (total_all + kEmitTile - 1) / kEmitTile;
   for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
     const uint32_t e0 = t * kEmitTile, e1 = min(e0 + uint32_t(kEmitTile), total);
-    const uint32_t p_lo = E.tile_start[t];
-    const uint32_t p_hi = (uint64_t(t) + 1 < ntile_all) ? E.tile_start[t + 1] : nvis - 1;
-    const int np = int(p_hi - p_lo) + 1;
+    const uint32_t p_lo = R.row_tstart[t];
+    const uint32_t p_hi = (uint64_t(t) + 1 < ntile_all) ? R.row_tstart[t + 1] : nvis - 1;
+    const int np = int(p_hi - p_lo) + 1;  // <= kEmitTile + 1: every pair has >= 1 row
     for (int j = threadIdx.x; j < np; j += blockDim.x) {
-      uint32_t pr = E.pairs[p_lo + j];
-      s_off[j] = E.off[p_lo + j];
-      s_pair[j] = pr;
-      s_rect[j] = E.rect[pr];
+      s_off[j] = R.row_off[p_lo + j];
+      s_pair[j] = R.pairs[p_lo + j];
     }
     __syncthreads();
     for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      int a = 0, b = np - 1;  // largest j with s_off[j] <= e
+      int a = 0, b = np - 1;
       while (a < b) {
         int m = (a + b + 1) >> 1;
         if (s_off[m] <= e) a = m; else b = m - 1;
       }
-      uint32_t k = e - s_off[a];
-      uint2 r = s_rect[a];
-      uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF;
-      uint32_t rw = tx1 - tx0 + 1;
-      uint32_t ty = ty0 + k / rw, tx = tx0 + k % rw;
-      uint32_t v = s_pair[a] / uint32_t(E.n);
-      const DevCam &cam = E.cams[v];
-      E.keys[e] = uint32_t(cam.tile_base) + ty * uint32_t(cam.tiles_x) + tx;
-      E.vals[e] = p_lo + uint32_t(a);
+      const uint32_t pair = s_pair[a];
+      const uint2 r = R.rect[pair];
+      const uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF;
+      const uint32_t ty = ty0 + (e - s_off[a]);
+      uint32_t xa_t = tx0, xb_t = tx1;
+      const Ell el = R.ell[pair];
+      bool empty = false;
+      if (el.rho >= 0.f) {
+        const DevCam &cam = R.cams[pair / uint32_t(R.n)];
+        const float ya = float(ty * R.tile_h) + 0.5f;
+        const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
+        float xa, xb;
+        if (!ellipse_band(el, ya - 0.02f, yb + 0.02f, xa, xb)) {
+          empty = true;
+        } else {
+          // pixel centres i + 0.5 in [xa, xb] (with a margin), as tile columns
+          const float fa = ceilf(fminf(fmaxf(xa - 0.52f, -1.f), 65536.f * R.tile_w));
+          const float fb = floorf(fminf(fmaxf(xb - 0.48f, -1.f), 65536.f * R.tile_w));
+          if (fa > fb || fb < 0.f) {
+            empty = true;
+          } else {
+            const uint32_t ia = uint32_t(fmaxf(fa, 0.f)), ib = uint32_t(fb);
+            xa_t = max(tx0, ia / uint32_t(R.tile_w));
+            xb_t = min(tx1, ib / uint32_t(R.tile_w));
+            if (xa_t > xb_t) empty = true;
+          }
+        }
+      }
+      R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
+      R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const Counters *c, uint2 *ranges) {
-  const uint32_t n = c->n_inst_clamped;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t k = keys[i];
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
-  }
+cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st) {
+  rows_kernel<<<G, 256, 0, st>>>(R);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_count_scan(const ScanParams &S, int G, cudaStream_t st) {
-  count_tiles_kernel<<<G, 256, 0, st>>>(S);
-  scan_partials_kernel<<<1, 32, 0, st>>>(S, G);
-  offsets_kernel<<<G, 256, 0, st>>>(S);
-  return cudaGetLastError();
+// ------------------------------------------------------------------- emission
+__global__ void __launch_bounds__(256) emit_kernel(EmitParams E) {
+  __shared__ uint32_t s_off[kEmitTile + 1];
+  __shared__ uint2 s_seg[kEmitTile + 1];
+  const uint32_t total = E.counters->n_inst_clamped;
+  const unsigned long long total_all = E.counters->n_instances;
+  const uint32_t nrows = E.counters->n_rows_clamped;
+  const uint32_t ntile = (total + kEmitTile - 1) / kEmitTile;
+  const unsigned long long ntile_all = (total_all + kEmitTile - 1) / kEmitTile;
+  for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const uint32_t e0 = t * kEmitTile, e1 = min(e0 + uint32_t(kEmitTile), total);
+    const uint32_t r_lo = E.tile_start[t];
+    const uint32_t r_hi = (uint64_t(t) + 1 < ntile_all) ? E.tile_start[t + 1] : nrows - 1;
+    const int nr = int(r_hi - r_lo) + 1;
+    const bool in_smem = nr <= kEmitTile + 1;  // rows of zero length can make it larger
+    if (in_smem) {
+      for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        s_off[j] = E.seg_off[r_lo + j];
+        s_seg[j] = E.seg[r_lo + j];
+      }
+    }
+    __syncthreads();
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      int a = 0, b = nr - 1;  // largest row with offset <= e (a row of length 0 never wins)
+      while (a < b) {
+        int m = (a + b + 1) >> 1;
+        uint32_t om = in_smem ? s_off[m] : E.seg_off[r_lo + m];
+        if (om <= e) a = m; else b = m - 1;
+      }
+      const uint2 sg = in_smem ? s_seg[a] : E.seg[r_lo + a];
+      const uint32_t off = in_smem ? s_off[a] : E.seg_off[r_lo + a];
+      const uint32_t pos = sg.x;
+      const uint32_t ty = sg.y & 0xFFFF, tx = (sg.y >> 16) + (e - off);
+      const DevCam &cam = E.cams[E.pairs[pos] / uint32_t(E.n)];
+      E.keys[e] = uint32_t(cam.tile_base) + ty * uint32_t(cam.tiles_x) + tx;
+      E.vals[e] = pos;
+    }
+    __syncthreads();
+  }
 }
 
 cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st) {
   emit_kernel<<<G, 256, 0, st>>>(E);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- tile ranges
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const Counters *c, uint2 *ranges) {
+  const uint32_t n = c->n_inst_clamped;
+  const uint32_t nq = (n + 3) / 4;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint32_t i0 = 4 * q;
+    uint32_t k[4];
+    if (i0 + 3 < n) {
+      uint4 v = *reinterpret_cast<const uint4 *>(keys + i0);
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0xFFFFFFFFu;
+    }
+    uint32_t prev = i0 == 0 ? 0xFFFFFFFFu : keys[i0 - 1];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = i0 + j;
+      if (i >= n) break;
+      if (i == 0 || prev != k[j]) {
+        ranges[k[j]].x = i;
+        if (i > 0) ranges[prev].y = i;
+      }
+      if (i == n - 1) ranges[k[j]].y = n;
+      prev = k[j];
+    }
+  }
 }
 
 cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st) {

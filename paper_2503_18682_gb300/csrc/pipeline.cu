@@ -1,0 +1,272 @@
+// Workspace layout and the order of kernel launches of the three hot-path stages, shared
+// by the plan API (caller-owned workspace) and the allocation-free entry point.
+#include <cmath>
+
+#include "raygs_internal.cuh"
+
+namespace raygs {
+
+namespace {
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+void fill_devcam(const raygs_camera &c, const raygs_config &cfg, DevCam &d) {
+  d = DevCam{};
+  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+  d.ifx = float(1.0 / double(c.fx));
+  d.ify = float(1.0 / double(c.fy));
+  d.W = c.width; d.H = c.height;
+  for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
+  for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
+  d.near_z = c.near_z;
+  d.mip = c.mip ? 1 : 0;
+  for (int k = 0; k < 3; ++k)
+    d.C[k] = float(-(double(c.R[k]) * c.t[0] + double(c.R[3 + k]) * c.t[1] + double(c.R[6 + k]) * c.t[2]));
+  d.xmin = float((0.5 - double(c.cx)) / double(c.fx));
+  d.xmax = float((double(c.width) - 0.5 - double(c.cx)) / double(c.fx));
+  d.ymin = float((0.5 - double(c.cy)) / double(c.fy));
+  d.ymax = float((double(c.height) - 0.5 - double(c.cy)) / double(c.fy));
+  d.tiles_x = (c.width + cfg.tile_w - 1) / cfg.tile_w;
+  d.tiles_y = (c.height + cfg.tile_h - 1) / cfg.tile_h;
+}
+
+bool config_valid(const raygs_config &cfg) {
+  const bool tile_ok = (cfg.tile_w == 16 && cfg.tile_h == 16) || (cfg.tile_w == 16 && cfg.tile_h == 8) ||
+                       (cfg.tile_w == 32 && cfg.tile_h == 16) || (cfg.tile_w == 8 && cfg.tile_h == 8);
+  return tile_ok && cfg.p_min > 0.f && cfg.p_min < 1.f && cfg.t_stop >= 0.f && cfg.t_stop < 1.f &&
+         cfg.alpha_max > 0.f && cfg.alpha_max < 1.f && cfg.mip_sigma2 >= 0.f && cfg.degenerate_ratio > 1.f &&
+         cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2;
+}
+
+bool camera_valid(const raygs_camera &c) {
+  return c.width >= 1 && c.height >= 1 && c.width <= 32768 && c.height <= 32768 && c.fx > 0.f && c.fy > 0.f &&
+         std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy) &&
+         c.near_z > 0.f;
+}
+
+raygs_status scene_valid(const raygs_scene *s, int64_t n) {
+  if (!s || s->n != n) return RAYGS_ERR_INVALID_ARG;
+  if (s->sh_degree < 0 || s->sh_degree > 3) return RAYGS_ERR_INVALID_ARG;
+  auto dt_ok = [](int d, bool allow_bf16) {
+    return d == RAYGS_F32 || d == RAYGS_F16 || (allow_bf16 && d == RAYGS_BF16);
+  };
+  if (!dt_ok(s->scale_dtype, true) || !dt_ok(s->opacity_dtype, false) || !dt_ok(s->sh_dtype, true))
+    return RAYGS_ERR_INVALID_ARG;
+  auto a16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (s->n > 0) {
+    if (!s->means || !s->log_scales || !s->quats || !s->opacity_logits || !s->sh) return RAYGS_ERR_INVALID_ARG;
+    if (!a16(s->means) || !a16(s->log_scales) || !a16(s->quats) || !a16(s->opacity_logits) || !a16(s->sh))
+      return RAYGS_ERR_INVALID_ARG;
+  }
+  return RAYGS_OK;
+}
+
+int sort_grid(int num_sms) {
+  int g = 4 * num_sms;
+  return g > 1024 ? 1024 : (g < 1 ? 1 : g);
+}
+
+int tile_sort_bits(int64_t tiles) {
+  int b = 1;
+  while (b < 32 && (int64_t(1) << b) < tiles) ++b;
+  return b;
+}
+
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = up256(o + bytes); return r; };
+  const size_t VN = size_t(n_views) * size_t(n);
+  const size_t C = size_t(cap);
+  L.cams = take(sizeof(DevCam) * size_t(n_views));
+  L.counters = take(sizeof(Counters));
+  L.evals = take(2 * sizeof(unsigned long long));
+  L.depth = take(4 * VN);
+  L.rect = take(8 * VN);
+  L.ell = take(sizeof(Ell) * VN);
+  L.rec = take(sizeof(Rec) * VN);
+  for (int i = 0; i < 2; ++i) { L.s1k[i] = take(4 * VN); L.s1v[i] = take(4 * VN); }
+  L.cnt = take(4 * VN);
+  L.off = take(4 * VN);
+  L.partial = take(4 * size_t(G));
+  L.rtstart_len = uint32_t(C / kEmitTile + 2);
+  L.rtstart = take(4 * size_t(L.rtstart_len));
+  L.seg = take(8 * C + 16);
+  L.seg_len = take(4 * C + 16);
+  L.seg_off = take(4 * C + 16);
+  L.itstart_len = uint32_t(C / kEmitTile + 2);
+  L.itstart = take(4 * size_t(L.itstart_len));
+  for (int i = 0; i < 2; ++i) { L.ik[i] = take(4 * C + 16); L.iv[i] = take(4 * C + 16); }
+  L.hist = take(4 * 512 * size_t(G));
+  L.ranges = take(8 * size_t(tiles));
+  L.deg = take(4 * VN);
+  L.degc = take(4);
+  L.total = o;
+  return L;
+}
+
+cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(w.base + w.L.counters, 0, sizeof(Counters), st);
+  if (e != cudaSuccess) return e;
+  PrepParams P;
+  P.means = scene.means;
+  P.log_scales = scene.log_scales;
+  P.quats = scene.quats;
+  P.logits = scene.opacity_logits;
+  P.sh = scene.sh;
+  P.sh_degree = scene.sh_degree;
+  P.scale_dtype = scene.scale_dtype;
+  P.opacity_dtype = scene.opacity_dtype;
+  P.sh_dtype = scene.sh_dtype;
+  P.n = int(w.n);
+  P.n_views = w.n_views;
+  P.cams = w.at<DevCam>(w.L.cams);
+  P.p_min = w.cfg.p_min;
+  P.mip_sigma2 = w.cfg.mip_sigma2;
+  P.degenerate_ratio = w.cfg.degenerate_ratio;
+  P.fp64_degenerate = w.cfg.fp64_degenerate;
+  P.tile_w = w.cfg.tile_w;
+  P.tile_h = w.cfg.tile_h;
+  P.depth_key = w.at<uint32_t>(w.L.depth);
+  P.rect = w.at<uint2>(w.L.rect);
+  P.ell = w.at<Ell>(w.L.ell);
+  P.rec = w.at<Rec>(w.L.rec);
+  P.counters = w.at<Counters>(w.L.counters);
+  P.deg_list = w.at<uint32_t>(w.L.deg);
+  P.deg_count = w.at<uint32_t>(w.L.degc);
+  return launch_preprocess(P, w.num_sms, st);
+}
+
+cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
+  Counters *ctr = w.at<Counters>(w.L.counters);
+  const uint32_t VN = uint32_t(size_t(w.n_views) * size_t(w.n));
+  const uint32_t cap = uint32_t(w.cap);
+  uint32_t *hist = w.at<uint32_t>(w.L.hist);
+  cudaError_t e;
+  // 1. depth sort of the visible pairs: 4 passes of 8 bits over the float32 key
+  int cur = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    SortPass sp;
+    sp.keys_in = w.at<uint32_t>(pass == 0 ? w.L.depth : w.L.s1k[cur]);
+    sp.vals_in = pass == 0 ? nullptr : w.at<uint32_t>(w.L.s1v[cur]);
+    const int dst = pass == 0 ? 0 : 1 - cur;
+    sp.keys_out = w.at<uint32_t>(w.L.s1k[dst]);
+    sp.vals_out = w.at<uint32_t>(w.L.s1v[dst]);
+    sp.d_count = pass == 0 ? nullptr : &ctr->n_visible;
+    sp.count_max = VN;
+    sp.shift = 8 * pass;
+    sp.bits = 8;
+    sp.filter = pass == 0 ? 1 : 0;
+    sp.hist = hist;
+    sp.G = w.G;
+    sp.d_total = pass == 0 ? &ctr->n_visible : nullptr;
+    if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
+    cur = dst;
+  }
+  w.s1_final = cur;
+  const uint32_t *pairs = w.at<uint32_t>(w.L.s1v[cur]);
+  // 2a. pairs -> tile rows
+  if ((e = launch_count_rows(pairs, w.at<uint2>(w.L.rect), w.at<uint32_t>(w.L.cnt), ctr, w.G, st)) != cudaSuccess)
+    return e;
+  ScanJob J;
+  J.cnt = w.at<uint32_t>(w.L.cnt);
+  J.off = w.at<uint32_t>(w.L.off);
+  J.d_n = &ctr->n_visible;
+  J.partial = w.at<uint32_t>(w.L.partial);
+  J.tile_start = w.at<uint32_t>(w.L.rtstart);
+  J.tstart_len = w.L.rtstart_len;
+  J.d_total = &ctr->n_rows;
+  J.d_total_clamped = &ctr->n_rows_clamped;
+  J.cap = cap;
+  J.d_overflow = &ctr->overflow;
+  if ((e = launch_scan(J, w.G, st)) != cudaSuccess) return e;
+  // 2b. rows -> tile spans inside the support ellipse
+  RowsParams R;
+  R.pairs = pairs;
+  R.rect = w.at<uint2>(w.L.rect);
+  R.ell = w.at<Ell>(w.L.ell);
+  R.row_off = J.off;
+  R.row_tstart = J.tile_start;
+  R.cams = w.at<DevCam>(w.L.cams);
+  R.counters = ctr;
+  R.n = int(w.n);
+  R.tile_w = w.cfg.tile_w;
+  R.tile_h = w.cfg.tile_h;
+  R.seg = w.at<uint2>(w.L.seg);
+  R.seg_len = w.at<uint32_t>(w.L.seg_len);
+  if ((e = launch_rows(R, w.G, st)) != cudaSuccess) return e;
+  ScanJob J2;
+  J2.cnt = R.seg_len;
+  J2.off = w.at<uint32_t>(w.L.seg_off);
+  J2.d_n = &ctr->n_rows_clamped;
+  J2.partial = w.at<uint32_t>(w.L.partial);
+  J2.tile_start = w.at<uint32_t>(w.L.itstart);
+  J2.tstart_len = w.L.itstart_len;
+  J2.d_total = &ctr->n_instances;
+  J2.d_total_clamped = &ctr->n_inst_clamped;
+  J2.cap = cap;
+  J2.d_overflow = &ctr->overflow;
+  if ((e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
+  // 2c. rows -> instances (tile id, sorted pair position), in depth order
+  EmitParams E;
+  E.seg = R.seg;
+  E.seg_off = J2.off;
+  E.tile_start = J2.tile_start;
+  E.pairs = pairs;
+  E.cams = R.cams;
+  E.counters = ctr;
+  E.n = int(w.n);
+  E.keys = w.at<uint32_t>(w.L.ik[0]);
+  E.vals = w.at<uint32_t>(w.L.iv[0]);
+  if ((e = launch_emit(E, w.G, st)) != cudaSuccess) return e;
+  // 3. stable sort of instances by tile id (9-bit digits)
+  const int bits = tile_sort_bits(w.tiles);
+  const int passes = (bits + 8) / 9;
+  cur = 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    SortPass sp;
+    sp.keys_in = w.at<uint32_t>(w.L.ik[cur]);
+    sp.vals_in = w.at<uint32_t>(w.L.iv[cur]);
+    sp.keys_out = w.at<uint32_t>(w.L.ik[1 - cur]);
+    sp.vals_out = w.at<uint32_t>(w.L.iv[1 - cur]);
+    sp.d_count = &ctr->n_inst_clamped;
+    sp.count_max = cap;
+    sp.shift = 9 * pass;
+    sp.bits = 9;
+    sp.filter = 0;
+    sp.hist = hist;
+    sp.G = w.G;
+    sp.d_total = nullptr;
+    if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
+    cur = 1 - cur;
+  }
+  w.s2_final = cur;
+  // 4. tile ranges
+  uint2 *ranges = w.at<uint2>(w.L.ranges);
+  if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(w.tiles), st)) != cudaSuccess) return e;
+  return launch_ranges(w.at<uint32_t>(w.L.ik[cur]), ctr, ranges, w.G, st);
+}
+
+cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_contrib, bool count,
+                       cudaStream_t st) {
+  RenderParams P;
+  P.cams = w.at<DevCam>(w.L.cams);
+  P.n_views = w.n_views;
+  P.ranges = w.at<uint2>(w.L.ranges);
+  P.inst_vals = w.at<uint32_t>(w.L.iv[w.s2_final]);
+  P.pairs = w.at<uint32_t>(w.L.s1v[w.s1_final]);
+  P.rec = w.at<Rec>(w.L.rec);
+  P.t_stop = w.cfg.t_stop;
+  P.alpha_max = w.cfg.alpha_max;
+  P.rgb = rgb;
+  P.Tf = T_final;
+  P.ncontrib = n_contrib;
+  P.eval_counts = w.at<unsigned long long>(w.L.evals);
+  if (count) {
+    cudaError_t e = cudaMemsetAsync(P.eval_counts, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);
+}
+
+}  // namespace raygs

@@ -8,8 +8,10 @@
 //   rec        64-byte pixel record (see Rec): the factors of the fragment formula of
 //              Sec. 4.2 / App. A.4 in a form that is evaluated from the pixel ray
 //
-// Primitives whose scale ratio exceeds degenerate_ratio are skipped by the float32
-// kernel and handled by preprocess_fp64_kernel, which runs the same stage in FP64.
+// For primitives whose scale ratio exceeds degenerate_ratio, the float32 result of a view
+// is replaced by the same stage run in FP64 (preprocess_fp64_kernel) when the float32
+// solve is ill-conditioned in that view (the disk is seen nearly edge-on), or for every
+// visible view when fp64_degenerate == 2.
 #include "raygs_internal.cuh"
 
 namespace raygs {
@@ -37,6 +39,9 @@ __device__ __forceinline__ void quat_rot(T w, T x, T y, T z, T R[9]) {
 struct StageOut {
   float G[4], h[2], kp, c2h, lo2o;
   int tx0, ty0, tx1, ty1;
+  bool illcond;  // the 2x2 projected covariance lost more than 3 digits in its Cholesky
+  // support ellipse (p - u - dc)^T M (p - u - dc) <= rho in pixel offsets from the centre
+  float dc0, dc1, M00, M01, M11, rho, det;
 };
 
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
@@ -146,27 +151,6 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
     float v = float(T(cam.fy) * py / pz + T(cam.cy));
     xmn = fminf(xmn, u); xmx = fmaxf(xmx, u); ymn = fminf(ymn, v); ymx = fmaxf(ymx, v);
   }
-  int i0, i1, j0, j1;
-  if (full) {
-    i0 = 0; j0 = 0; i1 = cam.W - 1; j1 = cam.H - 1;
-  } else {
-    if (!(xmn <= xmx) || !(ymn <= ymx)) return false;  // NaN guard
-    const float lim = 1.0e8f;
-    float mgx = 1e-3f + 1e-5f * fmaxf(fabsf(xmn), fabsf(xmx));
-    float mgy = 1e-3f + 1e-5f * fmaxf(fabsf(ymn), fabsf(ymx));
-    // pixel centre i + 0.5 inside [xmn, xmx] (with a small conservative margin)
-    float fi0 = ceilf(fminf(fmaxf(xmn - 0.5f - mgx, -lim), lim));
-    float fi1 = floorf(fminf(fmaxf(xmx - 0.5f + mgx, -lim), lim));
-    float fj0 = ceilf(fminf(fmaxf(ymn - 0.5f - mgy, -lim), lim));
-    float fj1 = floorf(fminf(fmaxf(ymx - 0.5f + mgy, -lim), lim));
-    fi0 = fmaxf(fi0, 0.f); fj0 = fmaxf(fj0, 0.f);
-    fi1 = fminf(fi1, float(cam.W - 1)); fj1 = fminf(fj1, float(cam.H - 1));
-    if (fi0 > fi1 || fj0 > fj1) return false;
-    i0 = int(fi0); i1 = int(fi1); j0 = int(fj0); j1 = int(fj1);
-  }
-  out.tx0 = i0 / tile_w; out.tx1 = i1 / tile_w;
-  out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
-
   // ---- Per-pixel factors.  With y = K x, K = Q^-1 (App. A.4 steps g-i),
   // D = c^2 |y01|^2 / |y|^2, which is the fragment formula 1/(c^-2 + |Z a|^-2) with the
   // quad coordinate Z a = c U^T y01 / y2 read off the pixel ray.  The rows of K01 span the
@@ -191,7 +175,9 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   T a11 = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2];
   T l00 = t_sqrt(a00);
   T l10 = a01 / l00;
-  T l11 = t_sqrt(fmax(a11 - l10 * l10, a11 * T(1e-30)));
+  T schur = a11 - l10 * l10;
+  out.illcond = !(schur > T(1e-3) * a11);
+  T l11 = t_sqrt(fmax(schur, a11 * T(1e-30)));
   T f10 = l10 / l00;
   T k0[3] = {e1[0] / l00, e1[1] / l00, e1[2] / l00};
   T k1[3] = {(e2[0] - f10 * e1[0]) / l11, (e2[1] - f10 * e1[1]) / l11, (e2[2] - f10 * e1[2]) / l11};
@@ -209,6 +195,66 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   out.kp = float((c2 - kappa) / kappa);
   out.c2h = float(c2 * T(0.5 * 1.4426950408889634));
   out.lo2o = float(t_log(o) * T(1.4426950408889634));
+
+  // ---- Screen-space support: with delta = px - u (pixels), D <= kappa and y2 > 0 hold
+  // exactly when f(delta) = kp |G delta|^2 - (1 + h.delta)^2 <= 0, a conic
+  // delta^T M delta - 2 h.delta - 1 <= 0 with M = kp G^T G - h h^T.  When M is positive
+  // definite (and not too ill-conditioned for float32 use) the support is the ellipse
+  // (delta - dc)^T M (delta - dc) <= rho with dc = M^-1 h, rho = 1 + h.dc; its bounding box
+  // tightens the quad's, and binning tests tile rows against it.
+  {
+    const T g00 = k0[0] * T(cam.ifx) * scl, g01 = k0[1] * T(cam.ify) * scl;
+    const T g10 = k1[0] * T(cam.ifx) * scl, g11 = k1[1] * T(cam.ify) * scl;
+    const T hh0 = w0 * T(cam.ifx) * sh, hh1 = w1 * T(cam.ify) * sh;
+    const T kpt = (c2 - kappa) / kappa;
+    const T M00 = kpt * (g00 * g00 + g10 * g10) - hh0 * hh0;
+    const T M01 = kpt * (g00 * g01 + g10 * g11) - hh0 * hh1;
+    const T M11 = kpt * (g01 * g01 + g11 * g11) - hh1 * hh1;
+    const T det = M00 * M11 - M01 * M01;
+    out.rho = -1.f;
+    if (M00 > T(0) && M11 > T(0) && det > T(1e-4) * M00 * M11) {
+      const T dc0 = (M11 * hh0 - M01 * hh1) / det, dc1 = (M00 * hh1 - M01 * hh0) / det;
+      const T rho = T(1) + hh0 * dc0 + hh1 * dc1;
+      if (rho > T(0)) {
+        out.dc0 = float(dc0); out.dc1 = float(dc1);
+        out.M00 = float(M00); out.M01 = float(M01); out.M11 = float(M11);
+        out.rho = float(rho); out.det = float(det);
+        // a bounded support ellipse bounds the pixels even where the quad reaches
+        // behind the camera
+        const T ucx = T(cam.fx) * mu[0] / mu[2] + T(cam.cx) + dc0;
+        const T ucy = T(cam.fy) * mu[1] / mu[2] + T(cam.cy) + dc1;
+        const T hx = t_sqrt(rho * T(1.001) * M11 / det), hy = t_sqrt(rho * T(1.001) * M00 / det);
+        if (full) {
+          full = false;
+          xmn = float(ucx - hx); xmx = float(ucx + hx); ymn = float(ucy - hy); ymx = float(ucy + hy);
+        } else {
+          xmn = fmaxf(xmn, float(ucx - hx)); xmx = fminf(xmx, float(ucx + hx));
+          ymn = fmaxf(ymn, float(ucy - hy)); ymx = fminf(ymx, float(ucy + hy));
+        }
+      }
+    }
+  }
+  int i0, i1, j0, j1;
+  if (full) {
+    i0 = 0; j0 = 0; i1 = cam.W - 1; j1 = cam.H - 1;
+  } else {
+    if (!(xmn <= xmx) || !(ymn <= ymx)) return false;  // empty or NaN
+    const float lim = 1.0e8f;
+    float mgx = 1e-3f + 1e-5f * fmaxf(fabsf(xmn), fabsf(xmx));
+    float mgy = 1e-3f + 1e-5f * fmaxf(fabsf(ymn), fabsf(ymx));
+    // pixel centre i + 0.5 inside [xmn, xmx] (with a small conservative margin)
+    float fi0 = ceilf(fminf(fmaxf(xmn - 0.5f - mgx, -lim), lim));
+    float fi1 = floorf(fminf(fmaxf(xmx - 0.5f + mgx, -lim), lim));
+    float fj0 = ceilf(fminf(fmaxf(ymn - 0.5f - mgy, -lim), lim));
+    float fj1 = floorf(fminf(fmaxf(ymx - 0.5f + mgy, -lim), lim));
+    fi0 = fmaxf(fi0, 0.f); fj0 = fmaxf(fj0, 0.f);
+    fi1 = fminf(fi1, float(cam.W - 1)); fj1 = fminf(fj1, float(cam.H - 1));
+    if (fi0 > fi1 || fj0 > fj1) return false;
+    i0 = int(fi0); i1 = int(fi1); j0 = int(fj0); j1 = int(fj1);
+  }
+  out.tx0 = i0 / tile_w; out.tx1 = i1 / tile_w;
+  out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
+
   return true;
 }
 
@@ -324,6 +370,12 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   P.rec[idx] = r;
   P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
                            uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
+  Ell e;
+  e.cx = u.hi + so.dc0;
+  e.cy = v.hi + so.dc1;
+  e.a = so.M00; e.b = so.M01; e.d = so.M11;
+  e.rho = so.rho; e.det = so.det; e.pad = 0.f;
+  P.ell[idx] = e;
   P.depth_key[idx] = __float_as_uint(z);
 }
 
@@ -366,14 +418,9 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
     float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
     degenerate = (lmax - lmin) > logf(P.degenerate_ratio);
   }
-  if (!finite) atomicAdd(&P.counters->n_nonfinite, 1ull);
-  if (degenerate) {
-    uint32_t slot = atomicAdd(P.deg_count, 1u);
-    P.deg_list[slot] = uint32_t(g);
-  }
-  if (!finite || degenerate) {
-    if (!finite)
-      for (int v = 0; v < P.n_views; ++v) P.depth_key[int64_t(v) * P.n + g] = kCulled;
+  if (!finite) {
+    atomicAdd(&P.counters->n_nonfinite, 1ull);
+    for (int v = 0; v < P.n_views; ++v) P.depth_key[int64_t(v) * P.n + g] = kCulled;
     return;
   }
   float Rp[9];
@@ -399,48 +446,51 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
     float rgb[3];
     sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
     write_record(P, idx, cam, muc, so, rgb, z);
+    if (degenerate && (P.fp64_degenerate == 2 || so.illcond)) {
+      uint32_t slot = atomicAdd(P.deg_count, 1u);
+      P.deg_list[slot] = uint32_t(idx);
+    }
   }
 }
 
-// FP64 vertex stage for the primitives listed by preprocess_kernel (scale ratio above
-// degenerate_ratio).  Grid-stride over the device-side list.
+// FP64 vertex stage for the (view, primitive) pairs listed by preprocess_kernel.  The
+// float32 record, rectangle and key of each pair are overwritten.  Grid-stride over the
+// device-side list.
 template <int DEG>
 __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t count = *P.deg_count;
   for (uint32_t li = blockIdx.x * blockDim.x + threadIdx.x; li < count; li += gridDim.x * blockDim.x) {
-    const int g = int(P.deg_list[li]);
+    const int64_t idx = P.deg_list[li];
+    const int v = int(idx / P.n);
+    const int g = int(idx - int64_t(v) * P.n);
     const float mx = P.means[3 * int64_t(g)], my = P.means[3 * int64_t(g) + 1], mz = P.means[3 * int64_t(g) + 2];
     double ls[3], qd[4];
     for (int k = 0; k < 3; ++k) ls[k] = load_attr(P.log_scales, 3 * int64_t(g) + k, P.scale_dtype);
     for (int k = 0; k < 4; ++k) qd[k] = P.quats[4 * int64_t(g) + k];
     const double logit = load_attr(P.logits, g, P.opacity_dtype);
-    float coef[3 * K];
-    for (int k = 0; k < 3 * K; ++k) coef[k] = load_attr(P.sh, int64_t(g) * 3 * K + k, P.sh_dtype);
     double Rp[9];
     quat_rot<double>(qd[0], qd[1], qd[2], qd[3], Rp);
     const double s[3] = {exp(ls[0]), exp(ls[1]), exp(ls[2])};
     const double o = 1.0 / (1.0 + exp(-logit));
-    for (int v = 0; v < P.n_views; ++v) {
-      const DevCam &cam = P.cams[v];
-      const int64_t idx = int64_t(v) * P.n + g;
-      float z = depth_f32(cam, mx, my, mz);
-      if (!(z > cam.near_z)) { P.depth_key[idx] = kCulled; continue; }
-      df muc[3];
-      mean_cam_df(cam, mx, my, mz, muc);
-      const double mu[3] = {double(muc[0].hi) + double(muc[0].lo), double(muc[1].hi) + double(muc[1].lo),
-                            double(muc[2].hi) + double(muc[2].lo)};
-      StageOut so;
-      if (!view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
-        P.depth_key[idx] = kCulled;
-        continue;
-      }
-      float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
-      float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-      float rgb[3];
-      sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
-      write_record(P, idx, cam, muc, so, rgb, z);
+    const DevCam &cam = P.cams[v];
+    const float z = depth_f32(cam, mx, my, mz);
+    df muc[3];
+    mean_cam_df(cam, mx, my, mz, muc);
+    const double mu[3] = {double(muc[0].hi) + double(muc[0].lo), double(muc[1].hi) + double(muc[1].lo),
+                          double(muc[2].hi) + double(muc[2].lo)};
+    StageOut so;
+    if (!view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+      P.depth_key[idx] = kCulled;
+      continue;
     }
+    float coef[3 * K];
+    for (int k = 0; k < 3 * K; ++k) coef[k] = load_attr(P.sh, int64_t(g) * 3 * K + k, P.sh_dtype);
+    float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
+    float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float rgb[3];
+    sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
+    write_record(P, idx, cam, muc, so, rgb, z);
   }
 }
 

@@ -40,14 +40,26 @@ struct __align__(16) Rec {
   float4 a, b, c, d;
 };
 
-// Device-side counters (one per plan).
+// Device-side counters (one per workspace).
 struct Counters {
   uint32_t n_visible;       // valid (primitive, view) pairs after culling
+  uint32_t n_rows_clamped;  // min(tile rows, capacity)
   uint32_t n_inst_clamped;  // min(instances, capacity)
+  uint32_t overflow;        // rows or instances exceeded the capacity
+  unsigned long long n_rows;
   unsigned long long n_instances;
   unsigned long long n_nonfinite;
-  uint32_t overflow;
-  uint32_t pad[3];
+  uint32_t n_fp64;          // (primitive, view) pairs recomputed in FP64
+  uint32_t pad;
+};
+
+// Screen-space support ellipse of a (primitive, view): pixel centres p with
+// (p - c)^T [[a, b], [b, d]] (p - c) <= rho are exactly the rays with D <= kappa (up to
+// rounding).  rho < 0 marks a support that is not a bounded ellipse in the image (or is
+// too ill-conditioned in float32): binning then keeps the whole rectangle.
+struct __align__(16) Ell {
+  float cx, cy, a, b;
+  float d, rho, det, pad;
 };
 
 struct RasterCfg {
@@ -144,9 +156,10 @@ struct PrepParams {
   int tile_w, tile_h;
   uint32_t *depth_key;
   uint2 *rect;
+  Ell *ell;
   Rec *rec;
   Counters *counters;
-  uint32_t *deg_list;   // ids of primitives left to the FP64 kernel
+  uint32_t *deg_list;   // (view, primitive) pairs left to the FP64 kernel
   uint32_t *deg_count;
 };
 
@@ -158,32 +171,50 @@ struct SortPass {
   const uint32_t *d_count;  // device item count (nullable: count_max is used)
   uint32_t count_max;
   int shift;
+  int bits;                 // digit width of this pass (8 or 9)
   int filter;               // drop kCulled keys; value = item index
-  uint32_t *hist;           // [256][G]
+  uint32_t *hist;           // [512][G]
   int G;
   uint32_t *d_total;        // receives the number of items kept (nullable)
 };
 
-struct ScanParams {
-  const uint32_t *pairs;    // sorted pair ids
-  const uint2 *rect;        // per pair
-  uint32_t *cnt;            // per sorted position
-  uint32_t *off;            // per sorted position (exclusive scan)
+// Exclusive scan of per-unit output counts, with the unit that holds the first output of
+// every block of kEmitTile outputs (load-balanced expansion).
+struct ScanJob {
+  const uint32_t *cnt;
+  uint32_t *off;
+  const uint32_t *d_n;      // number of units (device)
   uint32_t *partial;        // [G]
-  uint32_t *tile_start;     // first sorted position of each emit tile
-  Counters *counters;
-  uint32_t capacity;
-  uint32_t tile_start_len;  // entries of tile_start
+  uint32_t *tile_start;
+  uint32_t tstart_len;
+  unsigned long long *d_total;
+  uint32_t *d_total_clamped;
+  uint32_t cap;
+  uint32_t *d_overflow;
 };
 
-struct EmitParams {
-  const uint32_t *pairs;
+struct RowsParams {
+  const uint32_t *pairs;    // sorted pair ids
   const uint2 *rect;
-  const uint32_t *off;
-  const uint32_t *tile_start;
+  const Ell *ell;
+  const uint32_t *row_off;
+  const uint32_t *row_tstart;
   const DevCam *cams;
   const Counters *counters;
   int n;                    // primitives per view
+  int tile_w, tile_h;
+  uint2 *seg;               // per row: (sorted pair position, ty | txa << 16)
+  uint32_t *seg_len;        // per row: tiles of the row inside the support
+};
+
+struct EmitParams {
+  const uint2 *seg;
+  const uint32_t *seg_off;
+  const uint32_t *tile_start;
+  const uint32_t *pairs;
+  const DevCam *cams;
+  const Counters *counters;
+  int n;
   uint32_t *keys;           // [capacity] global tile id
   uint32_t *vals;           // [capacity] sorted pair position
 };
@@ -209,10 +240,49 @@ void note_cuda_error(cudaError_t e);
 
 cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st);
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
-cudaError_t launch_count_scan(const ScanParams &S, int G, cudaStream_t st);
+cudaError_t launch_count_rows(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt, const Counters *c, int G,
+                              cudaStream_t st);
+cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
+cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
 cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
                           cudaStream_t st);
+
+// ---------------------------------------------------------------- workspace
+// Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
+struct Layout {
+  size_t cams, counters, evals, depth, rect, ell, rec, s1k[2], s1v[2], cnt, off, partial, rtstart,
+      seg, seg_len, seg_off, itstart, ik[2], iv[2], hist, ranges, deg, degc, total;
+  uint32_t rtstart_len, itstart_len;
+};
+
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G);
+
+// A bound workspace and the sizes it was laid out for.
+struct Work {
+  char *base = nullptr;
+  Layout L{};
+  int n_views = 0;
+  int64_t n = 0, tiles = 0, cap = 0;
+  int G = 0, num_sms = 0;
+  raygs_config cfg{};
+  int s1_final = 0, s2_final = 0;  // which ping-pong buffers hold the sorted results
+  template <typename T>
+  T *at(size_t off) const { return reinterpret_cast<T *>(base + off); }
+};
+
+// Host-side helpers shared by the entry points.
+void fill_devcam(const raygs_camera &c, const raygs_config &cfg, DevCam &d);
+bool config_valid(const raygs_config &cfg);
+bool camera_valid(const raygs_camera &c);
+raygs_status scene_valid(const raygs_scene *s, int64_t n);
+
+int sort_grid(int num_sms);
+int tile_sort_bits(int64_t tiles);
+cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st);
+cudaError_t run_bin_sort(Work &w, cudaStream_t st);
+cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_contrib, bool count,
+                       cudaStream_t st);
 
 }  // namespace raygs

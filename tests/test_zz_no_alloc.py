@@ -57,7 +57,7 @@ def test_noalloc_matches_plan_render_twice(rg):
 
 def test_noalloc_rejects_scene_beyond_scratch(rg):
     import torch
-    n = 400_000   # ~100 bytes per (primitive, view) -> more than the 32 MiB array
+    n = 400_000   # ~140 bytes per (primitive, view) -> more than the 32 MiB array
     scene = scenes.uniform_scene(n, seed=32)
     st = rg.scene_to_device(scene)
     cams = [scenes.make_camera(32, 32, 32.0, 32.0)]
