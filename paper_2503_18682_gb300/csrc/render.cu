@@ -1,25 +1,29 @@
 // Per-tile rasterisation and front-to-back compositing (Sec. 3 Eq. rendering and
 // Eq. rend_opacity; Sec. 4.2 fragment formula).
 //
-// One CTA per screen tile of any view; one thread per pixel.  The tile's instance list
-// (depth order) is consumed in batches: each thread stages one 64-byte record in shared
-// memory, converting the projected centre to a tile-relative offset in double-float so
-// that per-pixel offsets stay exact to float32 rounding of the offset itself.  Per pixel:
-//   y01 = G (px - u), y2 = 1 + h . (px - u), q = |y01|^2, r = y2^2
-//   contributes iff y2 > 0 and kp q <= r           (D <= kappa, Eq. support)
-//   D log2(e)/2 = c2h q / (q + r)                   (fragment formula)
+// One CTA per screen tile of any view; each thread shades PX consecutive pixels of a
+// tile row.  The tile's instance list (depth order) is consumed in batches: each thread
+// stages records in shared memory, converting the projected centre to a tile-relative
+// offset in double-float so that per-pixel offsets stay exact to the float32 rounding of
+// the offset itself.  Per pixel, with delta = pixel centre - projected centre:
+//   y01 = G delta, y2 = 1 + h . delta, q = |y01|^2, r = y2^2
+//   contributes iff y2 > 0 and kp q - r <= 0          (D <= kappa, Eq. support)
+//   D log2(e)/2 = c2h q / (q + r)                     (fragment formula)
 //   omega = min(alpha_max, 2^(log2 o - D log2(e)/2))
-// Compositing stops before a primitive that would take T below t_stop; a CTA leaves the
-// list as soon as every pixel has stopped.
+// The PX pixels of a thread share the row term of y and step the column term by one
+// pixel (y += G[:,0]).  Compositing of a pixel stops before a primitive that would take T
+// below t_stop; a thread skips records once its pixels have all stopped, and the CTA
+// leaves the list once every thread has.
 #include "raygs_internal.cuh"
 
 namespace raygs {
 
-
-template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW *TH) render_kernel(RenderParams P) {
-  constexpr int NT = TW * TH;
-  __shared__ float4 s_A[NT], s_B[NT], s_C[NT], s_D[NT];
+template <int TW, int TH, int PX, bool COUNT>
+__global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
+  constexpr int NT = TW * TH / PX;  // threads
+  constexpr int NB = 2 * NT;        // records per batch
+  constexpr int QX = TW / PX;       // threads per tile row
+  __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
   __shared__ int s_view;
   const int tile = blockIdx.x;
   const int tid = threadIdx.x;
@@ -33,76 +37,100 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(RenderParams P) {
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
   const int px0 = tx * TW, py0 = ty * TH;
-  const int lx = tid % TW, ly = tid / TW;
+  const int lx = (tid % QX) * PX, ly = tid / QX;
   const int px = px0 + lx, py = py0 + ly;
-  const bool inside = px < cam.W && py < cam.H;
   const uint2 rg = P.ranges[tile];
   const float ox_tile = float(px0) + 0.5f, oy_tile = float(py0) + 0.5f;
   const float fl_x = float(lx), fl_y = float(ly);
 
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  int last = 0;
-  bool done = !inside;
+  float T[PX], C0[PX], C1[PX], C2[PX];
+  int last[PX];
+  uint32_t alive = 0;
+#pragma unroll
+  for (int k = 0; k < PX; ++k) {
+    T[k] = 1.f; C0[k] = 0.f; C1[k] = 0.f; C2[k] = 0.f; last[k] = 0;
+    if (py < cam.H && px + k < cam.W) alive |= 1u << k;
+  }
+  const uint32_t inside = alive;
   unsigned long long n_eval = 0, n_comp = 0;
 
-  for (uint32_t start = rg.x; start < rg.y; start += NT) {
-    if (__syncthreads_and(done)) break;
-    const uint32_t i = start + tid;
-    if (i < rg.y) {
-      const uint32_t pos = P.inst_vals[i];
-      const Rec r = P.rec[P.pairs[pos]];
-      df ox = two_sum(ox_tile, -r.a.x);
-      df oy = two_sum(oy_tile, -r.a.y);
-      s_A[tid] = make_float4(__fadd_rn(ox.hi, __fsub_rn(ox.lo, r.a.z)),
-                             __fadd_rn(oy.hi, __fsub_rn(oy.lo, r.a.w)), r.b.x, r.b.y);
-      s_B[tid] = make_float4(r.b.z, r.b.w, r.c.x, r.c.y);
-      s_C[tid] = make_float4(r.c.z, r.c.w, r.d.x, 0.f);
-      s_D[tid] = make_float4(r.d.y, r.d.z, r.d.w, 0.f);
+  for (uint32_t start = rg.x; start < rg.y; start += NB) {
+    if (__syncthreads_and(alive == 0)) break;
+#pragma unroll
+    for (int rr = 0; rr < NB / NT; ++rr) {
+      const int slot = tid + rr * NT;
+      const uint32_t i = start + slot;
+      if (i < rg.y) {
+        const Rec r = P.rec[P.pairs[P.inst_vals[i]]];
+        const df ox = two_sum(ox_tile, -r.a.x);
+        const df oy = two_sum(oy_tile, -r.a.y);
+        s_A[slot] = make_float4(__fadd_rn(ox.hi, __fsub_rn(ox.lo, r.a.z)),
+                                __fadd_rn(oy.hi, __fsub_rn(oy.lo, r.a.w)), r.b.x, r.b.y);
+        s_B[slot] = make_float4(r.b.z, r.b.w, r.c.x, r.c.y);
+        s_C[slot] = make_float4(r.c.z, r.c.w, r.d.x, 0.f);
+        s_D[slot] = make_float4(r.d.y, r.d.z, r.d.w, 0.f);
+      }
     }
     __syncthreads();
-    const int nb = min(NT, int(rg.y - start));
-    if (!done) {
-      int j = 0;
-      for (; j < nb; ++j) {
-        const float4 A = s_A[j], B = s_B[j];
-        const float dx = A.x + fl_x, dy = A.y + fl_y;
-        const float y0 = fmaf(A.z, dx, A.w * dy);
-        const float y1 = fmaf(B.x, dx, B.y * dy);
-        const float y2 = fmaf(B.z, dx, fmaf(B.w, dy, 1.f));
-        const float q = fmaf(y0, y0, y1 * y1);
-        const float rr = y2 * y2;
+    const int nb = min(NB, int(rg.y - start));
+    for (int j = 0; j < nb && alive; ++j) {
+      const float4 A = s_A[j], B = s_B[j];
+      const float kp = s_C[j].x;
+      const float dy = A.y + fl_y;
+      const float dx = A.x + fl_x;
+      float y0 = fmaf(A.z, dx, A.w * dy);
+      float y1 = fmaf(B.x, dx, B.y * dy);
+      float y2 = fmaf(B.z, dx, fmaf(B.w, dy, 1.f));
+      float q[PX], r[PX];
+      uint32_t hit = 0;
+#pragma unroll
+      for (int k = 0; k < PX; ++k) {
+        if (k) { y0 += A.z; y1 += B.x; y2 += B.z; }
+        q[k] = fmaf(y0, y0, y1 * y1);
+        r[k] = y2 * y2;
+        if (y2 > 0.f && fmaf(kp, q[k], -r[k]) <= 0.f) hit |= 1u << k;
+      }
+      if (COUNT) n_eval += __popc(alive);
+      hit &= alive;
+      if (hit) {
         const float4 Cc = s_C[j];
-        if (y2 > 0.f && Cc.x * q <= rr) {
-          const float E = Cc.y * __fdividef(q, q + rr);
-          const float al = fminf(P.alpha_max, ex2_approx(Cc.z - E));
-          const float Tn = T * (1.f - al);
-          if (Tn < P.t_stop) {
-            done = true;
-            break;
+        const float4 Dd = s_D[j];
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+          if (hit & (1u << k)) {
+            const float E = Cc.y * __fdividef(q[k], q[k] + r[k]);
+            const float al = fminf(P.alpha_max, ex2_approx(Cc.z - E));
+            const float Tn = T[k] * (1.f - al);
+            if (Tn < P.t_stop) {
+              alive &= ~(1u << k);
+            } else {
+              const float w = al * T[k];
+              C0[k] = fmaf(w, Dd.x, C0[k]);
+              C1[k] = fmaf(w, Dd.y, C1[k]);
+              C2[k] = fmaf(w, Dd.z, C2[k]);
+              T[k] = Tn;
+              last[k] = int(start - rg.x) + j + 1;
+              if (COUNT) ++n_comp;
+            }
           }
-          const float4 Dd = s_D[j];
-          const float w = al * T;
-          C0 = fmaf(w, Dd.x, C0);
-          C1 = fmaf(w, Dd.y, C1);
-          C2 = fmaf(w, Dd.z, C2);
-          T = Tn;
-          last = int(start - rg.x) + j + 1;
-          if (COUNT) ++n_comp;
         }
       }
-      if (COUNT) n_eval += (j < nb) ? j + 1 : nb;
     }
   }
   if (inside) {
     const long long pix = cam.pix_base + (long long)py * cam.W + px;
-    P.rgb[3 * pix] = C0;
-    P.rgb[3 * pix + 1] = C1;
-    P.rgb[3 * pix + 2] = C2;
-    if (P.Tf) P.Tf[pix] = T;
-    if (P.ncontrib) P.ncontrib[pix] = last;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+      if (inside & (1u << k)) {
+        P.rgb[3 * (pix + k)] = C0[k];
+        P.rgb[3 * (pix + k) + 1] = C1[k];
+        P.rgb[3 * (pix + k) + 2] = C2[k];
+        if (P.Tf) P.Tf[pix + k] = T[k];
+        if (P.ncontrib) P.ncontrib[pix + k] = last[k];
+      }
+    }
   }
   if (COUNT) {
-    // warp reduce, one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       n_eval += __shfl_down_sync(0xffffffffu, n_eval, o);
@@ -119,16 +147,16 @@ cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t
                           cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   const unsigned grid = unsigned(n_tiles);
-#define RAYGS_RENDER_CASE(TW, TH)                                                      \
+#define RAYGS_RENDER_CASE(TW, TH, PX)                                                  \
   if (tile_w == TW && tile_h == TH) {                                                  \
-    if (count) render_kernel<TW, TH, true><<<grid, TW * TH, 0, st>>>(P);               \
-    else render_kernel<TW, TH, false><<<grid, TW * TH, 0, st>>>(P);                    \
+    if (count) render_kernel<TW, TH, PX, true><<<grid, TW * TH / PX, 0, st>>>(P);      \
+    else render_kernel<TW, TH, PX, false><<<grid, TW * TH / PX, 0, st>>>(P);           \
     return cudaGetLastError();                                                         \
   }
-  RAYGS_RENDER_CASE(16, 16)
-  RAYGS_RENDER_CASE(16, 8)
-  RAYGS_RENDER_CASE(32, 16)
-  RAYGS_RENDER_CASE(8, 8)
+  RAYGS_RENDER_CASE(16, 16, 4)
+  RAYGS_RENDER_CASE(16, 8, 4)
+  RAYGS_RENDER_CASE(32, 16, 4)
+  RAYGS_RENDER_CASE(8, 8, 2)
 #undef RAYGS_RENDER_CASE
   return cudaErrorInvalidValue;
 }
