@@ -89,6 +89,7 @@ typedef struct {
                               the views where the float32 solve is ill-conditioned (seen
                               nearly edge-on); 2 in every view where they are visible */
   float degenerate_ratio; /* 1e3 */
+  int32_t enable_backward; /* 1: reserve workspace for raygs_render_backward (default 0) */
 } raygs_config;
 
 /* Device-side counters of the last preprocess / bin_sort / render sequence. */
@@ -187,10 +188,13 @@ raygs_status raygs_render(raygs_plan *plan, float *rgb, float *T_final, int32_t 
 
 /*
  * Gradients of a scalar loss L through raygs_render back to the scene parameters
- * (not in the paper, whose renderer is not differentiable).  Uses the workspace of the
- * preceding forward pass (same plan, scene unchanged).  dL_drgb [num_pixels][3] device
- * required; dL_dT [num_pixels] optional.  T_final and n_contrib are the forward outputs.
- * Gradient buffers are overwritten (not accumulated).
+ * (not in the paper, whose renderer is not differentiable; reverse mode of Eq. rendering,
+ * Eq. rend_opacity and Eq. Q_ray).  Uses the workspace of the preceding forward pass (same
+ * plan, scene unchanged, no instance overflow).  dL_drgb [num_pixels][3] device required;
+ * dL_dT [num_pixels] optional.  T_final and n_contrib are the forward outputs.  Gradient
+ * buffers are overwritten (not accumulated); gradients of views are summed.  Requires
+ * cfg.enable_backward (else RAYGS_ERR_STATE); views with the MIP filter are not
+ * differentiated (RAYGS_ERR_INVALID_ARG).
  */
 raygs_status raygs_render_backward(raygs_plan *plan, const raygs_scene *scene,
                                    const float *T_final, const int32_t *n_contrib,

@@ -41,6 +41,7 @@ void raygs_config_default(raygs_config *cfg) {
   cfg->tile_h = 16;
   cfg->fp64_degenerate = 1;
   cfg->degenerate_ratio = 1e3f;
+  cfg->enable_backward = 0;
 }
 
 const char *raygs_status_string(raygs_status s) {
@@ -97,7 +98,7 @@ raygs_status raygs_plan_create(const raygs_camera *cams, int32_t n_views, int64_
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  w.L = make_layout(n_views, n_gaussians, tb, max_instances, w.G);
+  w.L = make_layout(n_views, n_gaussians, tb, max_instances, w.G, cfg.enable_backward != 0);
   p->total_pixels = pb;
   *out = p;
   return RAYGS_OK;
@@ -244,9 +245,17 @@ raygs_status raygs_graph_launch(raygs_plan *plan, void *stream) {
 raygs_status raygs_render_backward(raygs_plan *plan, const raygs_scene *scene, const float *T_final,
                                    const int32_t *n_contrib, const float *dL_drgb, const float *dL_dT,
                                    const raygs_grads *grads, void *stream) {
-  (void)plan; (void)scene; (void)T_final; (void)n_contrib; (void)dL_drgb; (void)dL_dT; (void)grads;
-  (void)stream;
-  return RAYGS_ERR_STATE;
+  if (!plan || !plan->w.base || !T_final || !n_contrib || !dL_drgb || !grads) return RAYGS_ERR_INVALID_ARG;
+  if (!plan->w.cfg.enable_backward) return RAYGS_ERR_STATE;
+  if (plan->stage < 2) return RAYGS_ERR_STATE;
+  for (const raygs_camera &c : plan->cams)
+    if (c.mip) return RAYGS_ERR_INVALID_ARG;  // no derivative of the anti-aliasing term
+  raygs_status s = scene_valid(scene, plan->w.n);
+  if (s != RAYGS_OK) return s;
+  cudaError_t e = run_backward(plan->w, *scene, T_final, n_contrib, dL_drgb, dL_dT, *grads,
+                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return RAYGS_OK;
 }
 
 /* ------------------------------------------------------------------ diagnostics

@@ -56,6 +56,7 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   if (!cams || !scene || !rgb || n_views < 1 || n_views > RAYGS_MAX_VIEWS) return RAYGS_ERR_INVALID_ARG;
   raygs_config cfg;
   if (cfg_in) cfg = *cfg_in; else raygs_config_default(&cfg);
+  cfg.enable_backward = 0;
   if (!config_valid(cfg)) return RAYGS_ERR_INVALID_ARG;
   const int64_t n = scene->n;
   if (n < 0 || n >= (int64_t(1) << 31)) return RAYGS_ERR_INVALID_ARG;
@@ -90,13 +91,13 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  const Layout L0 = make_layout(n_views, n, tiles, 0, w.G);
+  const Layout L0 = make_layout(n_views, n, tiles, 0, w.G, false);
   if (L0.total + 8192 > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   int64_t cap = int64_t((kNoAllocScratchBytes - L0.total - 8192) / 37);
-  w.L = make_layout(n_views, n, tiles, cap, w.G);
+  w.L = make_layout(n_views, n, tiles, cap, w.G, false);
   while (w.L.total > kNoAllocScratchBytes && cap > 0) {
     cap -= 4096;
-    w.L = make_layout(n_views, n, tiles, cap, w.G);
+    w.L = make_layout(n_views, n, tiles, cap, w.G, false);
   }
   if (cap <= 0 || w.L.total > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   w.cap = cap;

@@ -35,7 +35,7 @@ bool config_valid(const raygs_config &cfg) {
                        (cfg.tile_w == 32 && cfg.tile_h == 16) || (cfg.tile_w == 8 && cfg.tile_h == 8);
   return tile_ok && cfg.p_min > 0.f && cfg.p_min < 1.f && cfg.t_stop >= 0.f && cfg.t_stop < 1.f &&
          cfg.alpha_max > 0.f && cfg.alpha_max < 1.f && cfg.mip_sigma2 >= 0.f && cfg.degenerate_ratio > 1.f &&
-         cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2;
+         cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2 && (cfg.enable_backward == 0 || cfg.enable_backward == 1);
 }
 
 bool camera_valid(const raygs_camera &c) {
@@ -72,7 +72,7 @@ int tile_sort_bits(int64_t tiles) {
   return b;
 }
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G) {
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bool backward) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = up256(o + bytes); return r; };
@@ -101,6 +101,8 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G) {
   L.ranges = take(8 * size_t(tiles));
   L.deg = take(4 * VN);
   L.degc = take(4);
+  L.partials = backward ? take(4 * kGradW * C + 16) : 0;
+  L.pg = backward ? take(4 * kGradW * VN + 16) : 0;
   L.total = o;
   return L;
 }
@@ -267,6 +269,62 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
     if (e != cudaSuccess) return e;
   }
   return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);
+}
+
+cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T_final, const int32_t *n_contrib,
+                         const float *dL_drgb, const float *dL_dT, const raygs_grads &grads, cudaStream_t st) {
+  BackParams B;
+  B.cams = w.at<DevCam>(w.L.cams);
+  B.n_views = w.n_views;
+  B.ranges = w.at<uint2>(w.L.ranges);
+  B.inst_vals = w.at<uint32_t>(w.L.iv[w.s2_final]);
+  B.pairs = w.at<uint32_t>(w.L.s1v[w.s1_final]);
+  B.rec = w.at<Rec>(w.L.rec);
+  B.rect = w.at<uint2>(w.L.rect);
+  B.row_off = w.at<uint32_t>(w.L.off);
+  B.seg = w.at<uint2>(w.L.seg);
+  B.seg_off = w.at<uint32_t>(w.L.seg_off);
+  B.t_stop = w.cfg.t_stop;
+  B.alpha_max = w.cfg.alpha_max;
+  B.Tf = T_final;
+  B.ncontrib = n_contrib;
+  B.dL_drgb = dL_drgb;
+  B.dL_dT = dL_dT;
+  B.partials = w.at<float>(w.L.partials);
+  cudaError_t e = launch_render_backward(B, w.cfg.tile_w, w.cfg.tile_h, w.tiles, st);
+  if (e != cudaSuccess) return e;
+  PairGradParams Q;
+  Q.pairs = B.pairs;
+  Q.row_off = B.row_off;
+  Q.seg_off = B.seg_off;
+  Q.counters = w.at<Counters>(w.L.counters);
+  Q.partials = B.partials;
+  Q.pg = w.at<float>(w.L.pg);
+  if ((e = launch_pair_grads(Q, w.G, st)) != cudaSuccess) return e;
+  ParamGradParams R;
+  R.means = scene.means;
+  R.log_scales = scene.log_scales;
+  R.quats = scene.quats;
+  R.logits = scene.opacity_logits;
+  R.sh = scene.sh;
+  R.sh_degree = scene.sh_degree;
+  R.scale_dtype = scene.scale_dtype;
+  R.opacity_dtype = scene.opacity_dtype;
+  R.sh_dtype = scene.sh_dtype;
+  R.n = int(w.n);
+  R.n_views = w.n_views;
+  R.cams = B.cams;
+  R.p_min = w.cfg.p_min;
+  R.degenerate_ratio = w.cfg.degenerate_ratio;
+  R.fp64_degenerate = w.cfg.fp64_degenerate;
+  R.depth_key = w.at<uint32_t>(w.L.depth);
+  R.pg = Q.pg;
+  R.d_means = grads.d_means;
+  R.d_log_scales = grads.d_log_scales;
+  R.d_quats = grads.d_quats;
+  R.d_logits = grads.d_opacity_logits;
+  R.d_sh = grads.d_sh;
+  return launch_param_grads(R, st);
 }
 
 }  // namespace raygs

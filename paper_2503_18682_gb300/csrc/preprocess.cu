@@ -13,28 +13,12 @@
 // solve is ill-conditioned in that view (the disk is seen nearly edge-on), or for every
 // visible view when fp64_degenerate == 2.
 #include "raygs_internal.cuh"
+#include "stage_math.cuh"
 
 namespace raygs {
 
 
 constexpr int kPrepThreads = 128;
-
-__device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double t_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float t_log(float x) { return logf(x); }
-__device__ __forceinline__ double t_log(double x) { return log(x); }
-__device__ __forceinline__ float t_exp(float x) { return expf(x); }
-__device__ __forceinline__ double t_exp(double x) { return exp(x); }
-
-// Rotation of a quaternion (w, x, y, z) after normalisation, closed-form matrix.
-template <typename T>
-__device__ __forceinline__ void quat_rot(T w, T x, T y, T z, T R[9]) {
-  T inv = T(1) / t_sqrt(w * w + x * x + y * y + z * z);
-  w *= inv; x *= inv; y *= inv; z *= inv;
-  R[0] = T(1) - T(2) * (y * y + z * z); R[1] = T(2) * (x * y - w * z); R[2] = T(2) * (x * z + w * y);
-  R[3] = T(2) * (x * y + w * z); R[4] = T(1) - T(2) * (x * x + z * z); R[5] = T(2) * (y * z - w * x);
-  R[6] = T(2) * (x * z - w * y); R[7] = T(2) * (y * z + w * x); R[8] = T(1) - T(2) * (x * x + y * y);
-}
 
 struct StageOut {
   float G[4], h[2], kp, c2h, lo2o;
@@ -157,30 +141,8 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   // Sigma-orthonormal complement of mu, built stably from an orthonormal basis E of the
   // plane orthogonal to mu: K01 = L^-1 E^T with L L^T = E^T Sigma E.  Since K01 mu = 0,
   // y01 only needs the pixel offset from the projected centre.
-  T nn = t_sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
-  T n0 = mu[0] / nn, n1 = mu[1] / nn, n2 = mu[2] / nn;
-  T sg = n2 >= T(0) ? T(1) : T(-1);
-  T ba = T(-1) / (sg + n2);
-  T bb = n0 * n1 * ba;
-  T e1[3] = {T(1) + sg * n0 * n0 * ba, sg * bb, -sg * n0};
-  T e2[3] = {bb, sg + n1 * n1 * ba, -n1};
-  T M0[3], M1[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    M0[k] = (e1[0] * Rc[k] + e1[1] * Rc[3 + k] + e1[2] * Rc[6 + k]) * s[k];
-    M1[k] = (e2[0] * Rc[k] + e2[1] * Rc[3 + k] + e2[2] * Rc[6 + k]) * s[k];
-  }
-  T a00 = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2];
-  T a01 = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
-  T a11 = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2];
-  T l00 = t_sqrt(a00);
-  T l10 = a01 / l00;
-  T schur = a11 - l10 * l10;
-  out.illcond = !(schur > T(1e-3) * a11);
-  T l11 = t_sqrt(fmax(schur, a11 * T(1e-30)));
-  T f10 = l10 / l00;
-  T k0[3] = {e1[0] / l00, e1[1] / l00, e1[2] / l00};
-  T k1[3] = {(e2[0] - f10 * e1[0]) / l11, (e2[1] - f10 * e1[1]) / l11, (e2[2] - f10 * e1[2]) / l11};
+  T k0[3], k1[3];
+  out.illcond = !plane_whitening<T>(mu, Rc, s, k0, k1);
   T scl = mu[2] / c;  // normalise so that y2 = 1 on the centre ray
   out.G[0] = float(k0[0] * T(cam.ifx) * scl);
   out.G[1] = float(k0[1] * T(cam.ify) * scl);
@@ -256,66 +218,6 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
 
   return true;
-}
-
-// Camera-frame mean in double-float: R mu + t with error-free products and sums.
-__device__ __forceinline__ void mean_cam_df(const DevCam &cam, float mx, float my, float mz, df out[3]) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    df acc = {cam.t[r], 0.f};
-    acc = df_add(acc, two_prod(cam.R[3 * r], mx));
-    acc = df_add(acc, two_prod(cam.R[3 * r + 1], my));
-    acc = df_add(acc, two_prod(cam.R[3 * r + 2], mz));
-    out[r] = acc;
-  }
-}
-
-// Depth key: the fused chain fmaf(R20, x, fmaf(R21, y, fmaf(R22, z, t2))) in float32.
-__device__ __forceinline__ float depth_f32(const DevCam &cam, float mx, float my, float mz) {
-  return __fmaf_rn(cam.R[6], mx, __fmaf_rn(cam.R[7], my, __fmaf_rn(cam.R[8], mz, cam.t[2])));
-}
-
-// Real spherical harmonics (no Condon-Shortley phase) of unit direction (x, y, z) applied
-// to coefficients coef[k*3 + ch] (stride-1 floats); the first coefficient is the colour.
-template <int DEG>
-__device__ __forceinline__ void sh_colour(const float *coef, float x, float y, float z, float rgb[3]) {
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) rgb[ch] = coef[ch];
-  if (DEG >= 1) {
-    const float c1 = 0.4886025119029199f;  // sqrt(3/(4 pi))
-    float Y[3] = {c1 * y, c1 * z, c1 * x};
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (1 + k) + ch], rgb[ch]);
-  }
-  if (DEG >= 2) {
-    const float c2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
-    const float c2b = 0.31539156525252005f;  // sqrt(5/(16 pi))
-    const float c2c = 0.5462742152960396f;   // sqrt(15/(16 pi))
-    float Y[5] = {c2a * x * y, c2a * y * z, c2b * (3.f * z * z - 1.f), c2a * x * z, c2c * (x * x - y * y)};
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (4 + k) + ch], rgb[ch]);
-  }
-  if (DEG >= 3) {
-    const float c3a = 0.5900435899266435f;  // sqrt(35/(32 pi))
-    const float c3b = 2.890611442640554f;   // sqrt(105/(4 pi))
-    const float c3c = 0.4570457994644658f;  // sqrt(21/(32 pi))
-    const float c3d = 0.3731763325901154f;  // sqrt(7/(16 pi))
-    const float c3e = 1.445305721320277f;   // sqrt(105/(16 pi))
-    float z2 = z * z;
-    float Y[7] = {c3a * y * (3.f * x * x - y * y), c3b * x * y * z, c3c * y * (5.f * z2 - 1.f),
-                  c3d * z * (5.f * z2 - 3.f), c3c * x * (5.f * z2 - 1.f), c3e * z * (x * x - y * y),
-                  c3a * x * (x * x - 3.f * y * y)};
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(Y[k], coef[3 * (9 + k) + ch], rgb[ch]);
-  }
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
 }
 
 // Cooperative copy of `count` consecutive attributes starting at element `first` of `src`

@@ -234,6 +234,51 @@ struct RenderParams {
 };
 
 constexpr int kEmitTile = 2048;
+constexpr int kGradW = 13;  // per-instance / per-pair gradient partials (see backward.cu)
+
+struct BackParams {
+  const DevCam *cams;
+  int n_views;
+  const uint2 *ranges;
+  const uint32_t *inst_vals;
+  const uint32_t *pairs;
+  const Rec *rec;
+  const uint2 *rect;
+  const uint32_t *row_off;
+  const uint2 *seg;
+  const uint32_t *seg_off;
+  float t_stop, alpha_max;
+  const float *Tf;
+  const int *ncontrib;
+  const float *dL_drgb;
+  const float *dL_dT;   // nullable
+  float *partials;      // [capacity][kGradW] by emission index
+};
+
+struct PairGradParams {
+  const uint32_t *pairs;
+  const uint32_t *row_off;
+  const uint32_t *seg_off;
+  const Counters *counters;
+  const float *partials;
+  float *pg;            // [V*N][kGradW] by pair id
+};
+
+struct ParamGradParams {
+  const float *means;
+  const void *log_scales;
+  const float *quats;
+  const void *logits;
+  const void *sh;
+  int sh_degree, scale_dtype, opacity_dtype, sh_dtype;
+  int n, n_views;
+  const DevCam *cams;
+  float p_min, degenerate_ratio;
+  int fp64_degenerate;
+  const uint32_t *depth_key;
+  const float *pg;
+  float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+};
 
 // Records e as the thread's last CUDA error (read back by raygs_last_cuda_error).
 void note_cuda_error(cudaError_t e);
@@ -248,16 +293,19 @@ cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
                           cudaStream_t st);
+cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
+cudaError_t launch_pair_grads(const PairGradParams &P, int G, cudaStream_t st);
+cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
 
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
   size_t cams, counters, evals, depth, rect, ell, rec, s1k[2], s1v[2], cnt, off, partial, rtstart,
-      seg, seg_len, seg_off, itstart, ik[2], iv[2], hist, ranges, deg, degc, total;
+      seg, seg_len, seg_off, itstart, ik[2], iv[2], hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len, itstart_len;
 };
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G);
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bool backward);
 
 // A bound workspace and the sizes it was laid out for.
 struct Work {
@@ -284,5 +332,7 @@ cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st);
 cudaError_t run_bin_sort(Work &w, cudaStream_t st);
 cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_contrib, bool count,
                        cudaStream_t st);
+cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T_final, const int32_t *n_contrib,
+                         const float *dL_drgb, const float *dL_dT, const raygs_grads &grads, cudaStream_t st);
 
 }  // namespace raygs

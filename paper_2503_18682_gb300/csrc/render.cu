@@ -15,6 +15,7 @@
 // below t_stop; a thread skips records once its pixels have all stopped, and the CTA
 // leaves the list once every thread has.
 #include "raygs_internal.cuh"
+#include "raster_math.cuh"
 
 namespace raygs {
 
@@ -62,34 +63,15 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
       const uint32_t i = start + slot;
       if (i < rg.y) {
         const Rec r = P.rec[P.pairs[P.inst_vals[i]]];
-        const df ox = two_sum(ox_tile, -r.a.x);
-        const df oy = two_sum(oy_tile, -r.a.y);
-        s_A[slot] = make_float4(__fadd_rn(ox.hi, __fsub_rn(ox.lo, r.a.z)),
-                                __fadd_rn(oy.hi, __fsub_rn(oy.lo, r.a.w)), r.b.x, r.b.y);
-        s_B[slot] = make_float4(r.b.z, r.b.w, r.c.x, r.c.y);
-        s_C[slot] = make_float4(r.c.z, r.c.w, r.d.x, 0.f);
-        s_D[slot] = make_float4(r.d.y, r.d.z, r.d.w, 0.f);
+        stage_record(r, ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
       }
     }
     __syncthreads();
     const int nb = min(NB, int(rg.y - start));
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
-      const float kp = s_C[j].x;
-      const float dy = A.y + fl_y;
-      const float dx = A.x + fl_x;
-      float y0 = fmaf(A.z, dx, A.w * dy);
-      float y1 = fmaf(B.x, dx, B.y * dy);
-      float y2 = fmaf(B.z, dx, fmaf(B.w, dy, 1.f));
-      float q[PX], r[PX];
-      uint32_t hit = 0;
-#pragma unroll
-      for (int k = 0; k < PX; ++k) {
-        if (k) { y0 += A.z; y1 += B.x; y2 += B.z; }
-        q[k] = fmaf(y0, y0, y1 * y1);
-        r[k] = y2 * y2;
-        if (y2 > 0.f && fmaf(kp, q[k], -r[k]) <= 0.f) hit |= 1u << k;
-      }
+      float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
+      uint32_t hit = eval_pixels<PX>(A, B, s_C[j].x, fl_x, fl_y, q, r, y0, y1, y2);
       if (COUNT) n_eval += __popc(alive);
       hit &= alive;
       if (hit) {
@@ -98,8 +80,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           if (hit & (1u << k)) {
-            const float E = Cc.y * __fdividef(q[k], q[k] + r[k]);
-            const float al = fminf(P.alpha_max, ex2_approx(Cc.z - E));
+            const float al = fminf(P.alpha_max, pixel_opacity(Cc, q[k], r[k]));
             const float Tn = T[k] * (1.f - al);
             if (Tn < P.t_stop) {
               alive &= ~(1u << k);

@@ -33,7 +33,8 @@ class Camera(C.Structure):
 class Config(C.Structure):
     _fields_ = [("p_min", C.c_float), ("t_stop", C.c_float), ("alpha_max", C.c_float),
                 ("mip_sigma2", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("fp64_degenerate", C.c_int32), ("degenerate_ratio", C.c_float)]
+                ("fp64_degenerate", C.c_int32), ("degenerate_ratio", C.c_float),
+                ("enable_backward", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -320,6 +321,34 @@ class Renderer:
         return rgb, T, nc
 
     def forward(self, scene_t: dict, rgb=None, T=None, nc=None, stream=None, check=True):
+        """preprocess + bin_sort + render (see _forward)."""
+        out = self._forward(scene_t, rgb, T, nc, stream, check)
+        self.forward_id = getattr(self, "forward_id", 0) + 1
+        return out
+
+    def backward(self, scene_t: dict, T, nc, dL_drgb, dL_dT=None, stream=None, forward_id=None):
+        """Gradients of the last forward's image (needs enable_backward=1).  Returns a dict
+        of float32 tensors shaped like the scene attributes."""
+        torch = _torch()
+        if forward_id is not None and forward_id != getattr(self, "forward_id", None):
+            raise RayGSError("backward must follow its own forward on this Renderer")
+        dev = self.device
+        n = self.n
+        k = (int(scene_t["sh_degree"]) + 1) ** 2
+        out = dict(means=torch.empty((n, 3), dtype=torch.float32, device=dev),
+                   log_scales=torch.empty((n, 3), dtype=torch.float32, device=dev),
+                   quats=torch.empty((n, 4), dtype=torch.float32, device=dev),
+                   opacity_logits=torch.empty((n,), dtype=torch.float32, device=dev),
+                   sh=torch.empty((n, k, 3), dtype=torch.float32, device=dev))
+        g = Grads()
+        g.d_means, g.d_log_scales, g.d_quats = (out["means"].data_ptr(), out["log_scales"].data_ptr(),
+                                                out["quats"].data_ptr())
+        g.d_opacity_logits, g.d_sh = out["opacity_logits"].data_ptr(), out["sh"].data_ptr()
+        raygs_render_backward(self.plan, make_scene(scene_t), T, nc, dL_drgb.contiguous(),
+                              dL_dT.contiguous() if dL_dT is not None else None, g, stream)
+        return out
+
+    def _forward(self, scene_t: dict, rgb=None, T=None, nc=None, stream=None, check=True):
         """preprocess + bin_sort + render.  With check=True the counters are read (one
         sync) and the plan is regrown and the call repeated if the instance capacity
         overflowed."""
@@ -356,3 +385,46 @@ class Renderer:
 
     def debug_buffer(self, which: int) -> int:
         return int(lib().raygs_debug_buffer(self.plan, which) or 0)
+
+
+# ------------------------------------------------------------------ autograd
+
+def _autograd_function():
+    torch = _torch()
+
+    class RenderFunction(torch.autograd.Function):
+        """Differentiable RayGS render through the C ABI (forward: raygs_preprocess +
+        raygs_bin_sort + raygs_render; backward: raygs_render_backward)."""
+
+        @staticmethod
+        def forward(ctx, renderer, sh_degree, means, log_scales, quats, opacity_logits, sh):
+            st = dict(means=means.detach().contiguous(), log_scales=log_scales.detach().contiguous(),
+                      quats=quats.detach().contiguous(), opacity_logits=opacity_logits.detach().contiguous(),
+                      sh=sh.detach().contiguous(), sh_degree=int(sh_degree))
+            rgb, T, nc = renderer.forward(st)
+            ctx.renderer, ctx.st, ctx.fid = renderer, st, renderer.forward_id
+            ctx.save_for_backward(T, nc)
+            ctx.mark_non_differentiable(nc)
+            return rgb, T, nc
+
+        @staticmethod
+        def backward(ctx, g_rgb, g_T, _g_nc):
+            T, nc = ctx.saved_tensors
+            g = ctx.renderer.backward(ctx.st, T, nc, g_rgb, g_T, forward_id=ctx.fid)
+            return (None, None, g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"])
+
+    return RenderFunction
+
+
+_RENDER_FN = None
+
+
+def render(renderer: "Renderer", params: dict):
+    """Differentiable render of torch parameters (means, log_scales, quats,
+    opacity_logits, sh, sh_degree) with a Renderer created with enable_backward=1.
+    Returns (rgb [P,3], T [P], n_contrib [P])."""
+    global _RENDER_FN
+    if _RENDER_FN is None:
+        _RENDER_FN = _autograd_function()
+    return _RENDER_FN.apply(renderer, int(params["sh_degree"]), params["means"], params["log_scales"],
+                            params["quats"], params["opacity_logits"], params["sh"])
