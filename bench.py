@@ -337,11 +337,71 @@ def run_ours(args, world, rank, local):
         e2e=dict(value=1e3 / e2e_ms, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h)),
         gpu_launches=int(gpu_launches),
     )
+    if not args.no_backward:
+        line["fwd_bwd"] = fwd_bwd_ms_per_view(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def fwd_bwd_ms_per_view(args, dev):
+    """Forward + backward of the 1.5M-primitive 1280x720 view (blob generator, seed 2):
+    preprocess, binning, rasteriser and the full backward to all parameters, with a fixed
+    upstream gradient (the sign of the image minus a uniform random target, i.e. an L1
+    loss).  CUDA events on the launching stream; W warm-up and K timed passes."""
+    import torch
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene, cams = scenes.workload_backward_720p()
+    st = raygs.scene_to_device(scene, dev)
+    r = raygs.Renderer(cams, scene["means"].shape[0], device=dev, enable_backward=1)
+    rgb, T, nc = r.forward(st)
+    r.capacity = int(r.last_counters["n_instances"] * 1.1 + 65536)
+    r._make_plan()
+    rgb, T, nc = r.forward(st)
+    target = torch.rand(rgb.shape, generator=torch.Generator(device="cpu").manual_seed(2)).to(dev)
+    g_rgb = torch.sign(rgb - target).contiguous()
+    sc = raygs.make_scene(st)
+    n = scene["means"].shape[0]
+    grads = {k: torch.empty((n, d), dtype=torch.float32, device=dev) for k, d in
+             (("means", 3), ("log_scales", 3), ("quats", 4))}
+    grads["opacity_logits"] = torch.empty(n, dtype=torch.float32, device=dev)
+    grads["sh"] = torch.empty(st["sh"].shape, dtype=torch.float32, device=dev)
+    G = raygs.Grads()
+    G.d_means, G.d_log_scales, G.d_quats = (grads["means"].data_ptr(), grads["log_scales"].data_ptr(),
+                                            grads["quats"].data_ptr())
+    G.d_opacity_logits, G.d_sh = grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr()
+
+    def step():
+        raygs.raygs_preprocess(r.plan, sc)
+        raygs.raygs_bin_sort(r.plan)
+        raygs.raygs_render(r.plan, rgb, T, nc)
+        raygs.raygs_render_backward(r.plan, sc, T, nc, g_rgb, None, G)
+
+    def only_fwd():
+        raygs.raygs_preprocess(r.plan, sc)
+        raygs.raygs_bin_sort(r.plan)
+        raygs.raygs_render(r.plan, rgb, T, nc)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = max(3, min(args.steps, 20))
+    fb = timed(step, k)
+    fw = timed(only_fwd, k)
+    return dict(ms_per_view=fb, forward_ms=fw, backward_ms=fb - fw, n_gaussians=int(n),
+                resolution="1280x720", n_instances=int(r.last_counters["n_instances"]),
+                loss="L1 vs uniform random target (fixed upstream gradient)")
 
 
 def main():
@@ -353,6 +413,7 @@ def main():
     ap.add_argument("--n", type=int, default=3_000_000)
     ap.add_argument("--ref-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
     ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720"])
     args = ap.parse_args()
