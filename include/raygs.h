@@ -217,6 +217,25 @@ raygs_status raygs_graph_capture(raygs_plan *plan, const raygs_scene *scene, flo
 /* Launch the captured graph on `stream`. */
 raygs_status raygs_graph_launch(raygs_plan *plan, void *stream);
 
+/*
+ * Autotuner for the batched launch: for every compiled tile shape (16x16, 16x8, 32x16,
+ * 8x8 pixels; the shared-memory batch is two records per thread of each shape), build a
+ * plan over `workspace` (caller-owned, at least raygs_autotune_workspace_bytes() bytes),
+ * run one untimed pass, skip the shape if its instances overflow `max_instances`, then time
+ * `iters` passes of preprocess + bin_sort + render with CUDA events on `stream`.  Writes the
+ * fastest shape into cfg_inout->tile_w/tile_h and, if ms_out is non-NULL, the mean time per
+ * pass of each shape into ms_out[0..3] (-1 when skipped).  Synchronises `stream`.
+ * Returns RAYGS_ERR_CAPACITY when no shape fits.  (Not in the paper.)
+ */
+raygs_status raygs_autotune(const raygs_camera *cams, int32_t n_views, const raygs_scene *scene,
+                            int64_t max_instances, raygs_config *cfg_inout, void *workspace, size_t bytes,
+                            float *rgb, float *T_final, int32_t *n_contrib, int32_t iters, void *stream,
+                            float *ms_out);
+
+/* Workspace bytes raygs_autotune needs: the largest plan over the candidate shapes. */
+size_t raygs_autotune_workspace_bytes(const raygs_camera *cams, int32_t n_views, int64_t n_gaussians,
+                                      int64_t max_instances, const raygs_config *cfg);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Bytes of the device array raygs_render_noalloc works in (32 MiB). */

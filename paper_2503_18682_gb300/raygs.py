@@ -79,6 +79,11 @@ _SIGS = [
     ("raygs_graph_capture", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     ("raygs_graph_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("raygs_autotune", C.c_int, [C.POINTER(Camera), C.c_int32, C.POINTER(Scene), C.c_int64,
+                                 C.POINTER(Config), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_float)]),
+    ("raygs_autotune_workspace_bytes", C.c_size_t, [C.POINTER(Camera), C.c_int32, C.c_int64, C.c_int64,
+                                                    C.POINTER(Config)]),
     ("raygs_render_noalloc", C.c_int, [C.POINTER(Camera), C.c_int32, C.POINTER(Scene),
                                        C.POINTER(Config), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
@@ -259,6 +264,44 @@ def raygs_graph_capture(plan, scene: Scene, rgb, T_final=None, n_contrib=None, s
 
 def raygs_graph_launch(plan, stream=None):
     _check(lib().raygs_graph_launch(plan, stream_ptr(stream)), "raygs_graph_launch")
+
+
+TILE_CANDIDATES = [(16, 16), (16, 8), (32, 16), (8, 8)]
+
+
+def raygs_autotune_workspace_bytes(cams, n_gaussians: int, max_instances: int, cfg: Config | None = None) -> int:
+    arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    return int(lib().raygs_autotune_workspace_bytes(arr, len(arr), int(n_gaussians), int(max_instances),
+                                                    C.byref(cfg) if cfg is not None else None))
+
+
+def raygs_autotune(cams, scene: Scene, max_instances: int, cfg: Config, workspace, rgb, T_final=None,
+                   n_contrib=None, iters: int = 3, stream=None):
+    """Pick the fastest tile shape (written into cfg); returns {shape: ms per pass}."""
+    arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    ms = (C.c_float * len(TILE_CANDIDATES))()
+    _check(lib().raygs_autotune(arr, len(arr), C.byref(scene), int(max_instances), C.byref(cfg),
+                                workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                rgb.data_ptr(), T_final.data_ptr() if T_final is not None else None,
+                                n_contrib.data_ptr() if n_contrib is not None else None, int(iters),
+                                stream_ptr(stream), ms), "raygs_autotune")
+    return {f"{w}x{h}": float(ms[i]) for i, (w, h) in enumerate(TILE_CANDIDATES)}
+
+
+def autotune(cams, scene_t: dict, capacity: int, device="cuda", iters: int = 3, **cfg_kw):
+    """Convenience: allocate the autotuning workspace, run raygs_autotune, return
+    (config kwargs of the fastest shape, timings)."""
+    torch = _torch()
+    cfg = make_config(**cfg_kw)
+    nb = raygs_autotune_workspace_bytes(cams, scene_t["means"].shape[0], capacity, cfg)
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    npx = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    rgb = torch.empty((npx, 3), dtype=torch.float32, device=device)
+    T = torch.empty(npx, dtype=torch.float32, device=device)
+    nc = torch.empty(npx, dtype=torch.int32, device=device)
+    times = raygs_autotune(cams, make_scene(scene_t), capacity, cfg, ws, rgb, T, nc, iters)
+    del ws
+    return dict(cfg_kw, tile_w=int(cfg.tile_w), tile_h=int(cfg.tile_h)), times
 
 
 def raygs_render_noalloc(cams, scene: Scene, cfg: Config | None, rgb, T_final=None, n_contrib=None,

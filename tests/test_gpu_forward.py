@@ -169,3 +169,18 @@ def test_full_size_mip_720p_sampled(oracle_lib):
     pix, idx = sample_pixels(cams[0], 1536, seed=5)
     orc = oracle_lib.render(scene, cams[0], pixels=pix)
     assert_parity(compare(rgb[idx], T[idx], orc))
+
+
+def test_autotuner_picks_a_compiled_shape(oracle_lib):
+    """raygs_autotune times every tile shape on the caller's scene and views; the chosen
+    shape renders the same image (oracle parity)."""
+    from paper_2503_18682_gb300 import raygs
+    scene = scenes.uniform_scene(3000, seed=13)
+    R1, t1 = scenes.look_at([0.4, -0.3, -0.5], [0.0, 0.0, 3.0])
+    cams = [scenes.make_camera(96, 72, 80.0, 80.0), scenes.make_camera(50, 41, 40.0, 40.0, R=R1, t=t1)]
+    st = raygs.scene_to_device(scene)
+    kw, times = raygs.autotune(cams, st, capacity=1 << 20)
+    assert (kw["tile_w"], kw["tile_h"]) in raygs.TILE_CANDIDATES
+    assert all(v > 0 for v in times.values()), times
+    assert times[f"{kw['tile_w']}x{kw['tile_h']}"] == min(times.values())
+    check_views(scene, cams, oracle_lib, tile_w=kw["tile_w"], tile_h=kw["tile_h"])
