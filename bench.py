@@ -205,7 +205,11 @@ def run_ours(args, world, rank, local):
         scene, cams = scenes.workload_stereo_batch(n=args.n)
     n = int(scene["means"].shape[0])
     st = raygs.scene_to_device(scene, dev)
-    r = raygs.Renderer(cams, n, device=dev)
+    tile_kw = {}
+    if args.tile:
+        tw, th = (int(x) for x in args.tile.lower().split("x"))
+        tile_kw = dict(tile_w=tw, tile_h=th)
+    r = raygs.Renderer(cams, n, device=dev, **(tile_kw if args.mode == "profile" else {}))
     if args.mode == "profile":
         # for ncu: size the plan once, then W + K direct pipeline passes, nothing else
         stream = torch.cuda.current_stream()
@@ -430,6 +434,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", default="", help="profile mode: tile shape WxH (default 16x16)")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
     ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720"])
     args = ap.parse_args()

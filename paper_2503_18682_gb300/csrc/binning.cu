@@ -13,16 +13,17 @@
 //
 // The radix sort is reduce-then-scan (upsweep histogram, one-CTA scan, downsweep
 // scatter) with persistent CTAs that own contiguous tile ranges: no CTA ever waits on
-// another.  Ranking inside a tile is stable (warp match + per-warp counters) and the
-// scatter goes through shared memory so that global writes are coalesced runs.
+// another.  The upsweep counts runs of equal digits per thread; ranking inside a tile is
+// stable (warp match + per-warp counters) and the scatter goes through shared memory so
+// that global writes are coalesced runs.
 #include "raygs_internal.cuh"
 
 namespace raygs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortIPT = 16;
-constexpr int kSortTile = kSortThreads * kSortIPT;  // 4096 items
+constexpr int kSortIPT = 8;
+constexpr int kSortTile = kSortThreads * kSortIPT;  // 2048 items
 
 __device__ __forceinline__ void cta_tiles(uint32_t count, uint32_t &lo, uint32_t &hi) {
   uint32_t ntiles = (count + kSortTile - 1) / kSortTile;
@@ -37,37 +38,47 @@ __device__ __forceinline__ uint32_t pass_count(const SortPass &p) {
   return p.d_count ? min(*p.d_count, p.count_max) : p.count_max;
 }
 
+// Digit histogram of the CTA's items.  Each thread counts 16 consecutive keys as runs of
+// equal digits (the tile-id passes see long runs: instances come in depth order, tile rows
+// in order) and adds each run once to its warp's shared histogram.
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) sort_upsweep(SortPass p) {
   constexpr int R = 1 << BITS;
+  constexpr int KPT = 16;  // keys per thread per step
   __shared__ uint32_t h[kSortWarps][R];
   for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
   uint32_t lo, hi;
   cta_tiles(pass_count(p), lo, hi);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (uint32_t base = lo; base < hi; base += kSortThreads * 4) {
-    uint32_t i = base + threadIdx.x * 4;
-    uint32_t k[4];
-    bool ok[4];
-    if (i + 3 < hi) {
-      uint4 v = *reinterpret_cast<const uint4 *>(p.keys_in + i);
-      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-      ok[0] = ok[1] = ok[2] = ok[3] = true;
+  const int warp = threadIdx.x >> 5;
+  for (uint32_t base = lo; base < hi; base += kSortThreads * KPT) {
+    const uint32_t i0 = base + threadIdx.x * KPT;
+    uint32_t k[KPT];
+    if (i0 + KPT <= hi) {
+#pragma unroll
+      for (int q = 0; q < KPT / 4; ++q) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p.keys_in + i0 + 4 * q);
+        k[4 * q] = v.x; k[4 * q + 1] = v.y; k[4 * q + 2] = v.z; k[4 * q + 3] = v.w;
+      }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        ok[j] = i + j < hi;
-        k[j] = ok[j] ? p.keys_in[i + j] : 0u;
+      for (int j = 0; j < KPT; ++j) k[j] = i0 + j < hi ? p.keys_in[i0 + j] : kCulled;
+    }
+    uint32_t cur = 0xFFFFFFFFu, cnt = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const bool valid = i0 + j < hi && !(p.filter && k[j] == kCulled);
+      if (!valid) continue;
+      const uint32_t d = (k[j] >> p.shift) & (R - 1);
+      if (d == cur) {
+        ++cnt;
+      } else {
+        if (cnt) atomicAdd(&h[warp][cur], cnt);
+        cur = d;
+        cnt = 1;
       }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      bool valid = ok[j] && !(p.filter && k[j] == kCulled);
-      uint32_t d = (k[j] >> p.shift) & (R - 1);
-      uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[warp][d], uint32_t(__popc(peers)));
-    }
+    if (cnt) atomicAdd(&h[warp][cur], cnt);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < R; d += kSortThreads) {
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
       uint32_t v = ok ? (p.filter ? idx : p.vals_in[idx]) : 0u;
       bool valid = ok && !(p.filter && k == kCulled);
       uint32_t d = (k >> p.shift) & (R - 1);
-      uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
       uint32_t c = valid ? s_cnt[warp][d] : 0u;
       __syncwarp();
       if (valid && lane == 31 - __clz(peers)) s_cnt[warp][d] = c + __popc(peers);
@@ -222,16 +233,68 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
   }
 }
 
-cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
-  if (p.bits == 9) {
-    sort_upsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
-    scan_single_cta<<<1, 1024, 0, st>>>(p.hist, 512 * p.G, p.d_total);
-    sort_downsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
-  } else {
-    sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
-    scan_single_cta<<<1, 1024, 0, st>>>(p.hist, 256 * p.G, p.d_total);
-    sort_downsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+// Exclusive scan of the digit-major histogram [R][G] in place, in three steps: per-block
+// sums (one block per 2048 entries), a scan of the block sums, and the block-local scans.
+constexpr int kHistBlock = 2048;
+
+__global__ void __launch_bounds__(256) hist_reduce_kernel(const uint32_t *hist, int n, uint32_t *bsum) {
+  __shared__ uint32_t ws[33];
+  const int b0 = blockIdx.x * kHistBlock;
+  uint32_t s = 0;
+  for (int i = b0 + threadIdx.x; i < min(b0 + kHistBlock, n); i += blockDim.x) s += hist[i];
+  uint32_t tot;
+  block_excl_scan(s, ws, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) hist_bsum_kernel(uint32_t *bsum, int nb, uint32_t *d_total) {
+  __shared__ uint32_t ws[33];
+  const int per = (nb + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(b + per, nb);
+  uint32_t s = 0;
+  for (int i = b; i < e; ++i) s += bsum[i];
+  uint32_t tot;
+  uint32_t run = block_excl_scan(s, ws, &tot);
+  for (int i = b; i < e; ++i) {
+    const uint32_t v = bsum[i];
+    bsum[i] = run;
+    run += v;
   }
+  if (d_total && threadIdx.x == 0) *d_total = tot;
+}
+
+__global__ void __launch_bounds__(256) hist_offsets_kernel(uint32_t *hist, int n, const uint32_t *bsum) {
+  __shared__ uint32_t ws[33];
+  const int b0 = blockIdx.x * kHistBlock;
+  constexpr int PER = kHistBlock / 256;
+  uint32_t v[PER], s = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = b0 + threadIdx.x * PER + j;
+    v[j] = i < n ? hist[i] : 0u;
+    s += v[j];
+  }
+  uint32_t tot;
+  uint32_t run = bsum[blockIdx.x] + block_excl_scan(s, ws, &tot);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = b0 + threadIdx.x * PER + j;
+    if (i < n) hist[i] = run;
+    run += v[j];
+  }
+}
+
+cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
+  const int n = (p.bits == 9 ? 512 : 256) * p.G;
+  const int nb = (n + kHistBlock - 1) / kHistBlock;
+  uint32_t *bsum = p.hist + n;  // scratch after the histogram (the layout reserves 512*G + G)
+  if (p.bits == 9) sort_upsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
+  else sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  hist_reduce_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
+  hist_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nb, p.d_total);
+  hist_offsets_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
+  if (p.bits == 9) sort_downsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
+  else sort_downsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 

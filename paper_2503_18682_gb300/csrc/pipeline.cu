@@ -97,7 +97,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bo
   L.itstart_len = uint32_t(C / kEmitTile + 2);
   L.itstart = take(4 * size_t(L.itstart_len));
   for (int i = 0; i < 2; ++i) { L.ik[i] = take(4 * C + 16); L.iv[i] = take(4 * C + 16); }
-  L.hist = take(4 * 512 * size_t(G));
+  L.hist = take(4 * 512 * size_t(G) + 4 * (512 * size_t(G) / 2048 + 1));
   L.ranges = take(8 * size_t(tiles));
   L.deg = take(4 * VN);
   L.degc = take(4);
