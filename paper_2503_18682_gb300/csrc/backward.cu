@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       const int pos = start + j;
       const float4 A = s_A[j], B = s_B[j];
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
-      const uint32_t hit = eval_pixels<PX>(A, B, s_C[j].x, fl_x, fl_y, q, r, y0, y1, y2);
+      const uint32_t hit = row_may_hit<PX>(A, B, s_C[j].x, s_D[j].w, fl_x, fl_y)
+                               ? eval_pixels<PX>(A, B, s_C[j].x, fl_x, fl_y, q, r, y0, y1, y2)
+                               : 0u;
       float acc[kGradW];
 #pragma unroll
       for (int c = 0; c < kGradW; ++c) acc[c] = 0.f;
@@ -184,7 +186,7 @@ cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, 
   }
   RAYGS_BWD_CASE(16, 16, 4)
   RAYGS_BWD_CASE(16, 8, 4)
-  RAYGS_BWD_CASE(32, 16, 4)
+  RAYGS_BWD_CASE(32, 16, 8)
   RAYGS_BWD_CASE(8, 8, 2)
 #undef RAYGS_BWD_CASE
   return cudaErrorInvalidValue;

@@ -70,9 +70,11 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
     const int nb = min(NB, int(rg.y - start));
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
-      float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
-      uint32_t hit = eval_pixels<PX>(A, B, s_C[j].x, fl_x, fl_y, q, r, y0, y1, y2);
+      const float kp = s_C[j].x;
       if (COUNT) n_eval += __popc(alive);
+      if (!row_may_hit<PX>(A, B, kp, s_D[j].w, fl_x, fl_y)) continue;
+      float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
+      uint32_t hit = eval_pixels<PX>(A, B, kp, fl_x, fl_y, q, r, y0, y1, y2);
       hit &= alive;
       if (hit) {
         const float4 Cc = s_C[j];
@@ -136,7 +138,7 @@ cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t
   }
   RAYGS_RENDER_CASE(16, 16, 4)
   RAYGS_RENDER_CASE(16, 8, 4)
-  RAYGS_RENDER_CASE(32, 16, 4)
+  RAYGS_RENDER_CASE(32, 16, 8)
   RAYGS_RENDER_CASE(8, 8, 2)
 #undef RAYGS_RENDER_CASE
   return cudaErrorInvalidValue;
