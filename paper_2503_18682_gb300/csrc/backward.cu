@@ -54,19 +54,19 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
   const int px0 = tx * TW, py0 = ty * TH;
-  const int lx = (tid % QX) * PX, ly = tid / QX;
+  const int lx = tid % QX, ly = tid / QX;
   const int px = px0 + lx, py = py0 + ly;
   const uint2 rg = P.ranges[tile];
   const float ox_tile = float(px0) + 0.5f, oy_tile = float(py0) + 0.5f;
-  const float fl_x = float(lx), fl_y = float(ly);
+  const float fl_x = float(lx), fl_y = float(ly), step = float(QX);
 
   float Tk[PX], Tfin[PX], S0[PX], S1[PX], S2[PX], g0[PX], g1[PX], g2[PX], gT[PX];
   int last[PX];
   int lmax = 0;
 #pragma unroll
   for (int k = 0; k < PX; ++k) {
-    const bool in = py < cam.H && px + k < cam.W;
-    const long long pix = cam.pix_base + (long long)py * cam.W + px + k;
+    const bool in = py < cam.H && px + k * QX < cam.W;
+    const long long pix = cam.pix_base + (long long)py * cam.W + px + k * QX;
     Tfin[k] = in ? P.Tf[pix] : 1.f;
     Tk[k] = Tfin[k];
     last[k] = in ? P.ncontrib[pix] : 0;
@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       const int pos = start + j;
       const float4 A = s_A[j], B = s_B[j];
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
-      const uint32_t hit = row_may_hit<PX>(A, B, s_C[j].x, s_D[j].w, fl_x, fl_y)
-                               ? eval_pixels<PX>(A, B, s_C[j].x, fl_x, fl_y, q, r, y0, y1, y2)
+      const float4 Cs = s_C[j];
+      const uint32_t hit = row_may_hit<PX>(A, B, Cs, s_D[j].w, fl_x, fl_y, step)
+                               ? eval_pixels<PX>(A, B, Cs.x, fl_x, fl_y, step, q, r, y0, y1, y2)
                                : 0u;
       float acc[kGradW];
 #pragma unroll
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
           if (!clamped) {
             const float dLdD = -0.5f * om * dLdw;
             acc[9] += dLdw * om;
-            const float inv = Cc.w / (q[k] + r[k]);
+            const float inv = sqrtf(Cc.y * (2.f / kLog2e)) / (q[k] + r[k]);
             const float rho0 = y2[k] * y0[k] * inv, rho1 = y2[k] * y1[k] * inv, rho2 = -q[k] * inv;
             acc[0] += dLdD * rho0;
             acc[1] += dLdD * rho1;

@@ -9,8 +9,11 @@ namespace raygs {
 // Staged record (shared-memory layout of one 64-byte Rec, tile-relative):
 //   A = (ox, oy, G00, G01)   ox, oy: tile origin pixel centre minus projected centre
 //   B = (G10, G11, h0, h1)
-//   C = (kp, c2h, lo2o, c)   c = sqrt(mu^T Sigma^-1 mu) (backward only)
-//   D = (r, g, b, 0)
+//   C = (kp, c2h, lo2o, sc)  sc = kp (G00^2 + G10^2) + h0^2
+//   D = (r, g, b, a2)        a2 = 2 (kp (G00^2 + G10^2) - h0^2)
+// Along a pixel row, f = kp q - r is a quadratic in the column with second derivative a2,
+// and kp q + r (the magnitude that bounds the rounding of f) grows by at most sc per
+// column squared.
 __device__ __forceinline__ void stage_record(const Rec &r, float ox_tile, float oy_tile, float4 &A, float4 &B,
                                              float4 &C, float4 &D) {
   const df ox = two_sum(ox_tile, -r.a.x);
@@ -18,52 +21,60 @@ __device__ __forceinline__ void stage_record(const Rec &r, float ox_tile, float 
   A = make_float4(__fadd_rn(ox.hi, __fsub_rn(ox.lo, r.a.z)), __fadd_rn(oy.hi, __fsub_rn(oy.lo, r.a.w)), r.b.x,
                   r.b.y);
   B = make_float4(r.b.z, r.b.w, r.c.x, r.c.y);
-  C = make_float4(r.c.z, r.c.w, r.d.x, sqrtf(r.c.w * (2.0f / kLog2e)));
-  // second difference of f = kp q - r along a pixel row (constant: f is quadratic)
-  const float a2 = 2.f * fmaf(r.c.z, fmaf(r.b.x, r.b.x, r.b.z * r.b.z), -r.c.x * r.c.x);
-  D = make_float4(r.d.y, r.d.z, r.d.w, a2);
+  const float gg = fmaf(r.b.x, r.b.x, r.b.z * r.b.z);
+  const float hh = r.c.x * r.c.x;
+  C = make_float4(r.c.z, r.c.w, r.d.x, fmaf(r.c.z, gg, hh));
+  D = make_float4(r.d.y, r.d.z, r.d.w, 2.f * fmaf(r.c.z, gg, -hh));
 }
 
-// Conservative row filter: f = kp q - r (<= 0 exactly on the support, with y2 > 0) at PX
-// consecutive pixels by forward differences, f_{k+1} = f_k + d_k, d_{k+1} = d_k + a2.
-// Returns false only when every pixel is outside the support by more than the rounding
-// error of the recurrence; the exact per-pixel test (eval_pixels) decides otherwise.
+// Conservative segment filter.  A thread's PX pixels lie on one row at columns
+// fl_x + k s (k = 0 .. PX-1).  With t = k / (PX-1), f(t) = f0 + G1 t + A2 t^2 / 2 exactly,
+// so the minimum of f over the segment is f0, f(1) or, when the vertex lies inside,
+// f0 - G1^2 / (2 A2).  Returns false only when that minimum exceeds a margin that bounds
+// the float rounding of f at every pixel (each pixel's kp q + r is at most
+// 2 (kp q0 + r0) + 2 (s (PX-1))^2 sc); the exact per-pixel test (eval_pixels) decides
+// otherwise, so skipping never changes a result.
 template <int PX>
-__device__ __forceinline__ bool row_may_hit(const float4 &A, const float4 &B, float kp, float a2, float fl_x,
-                                            float fl_y) {
+__device__ __forceinline__ bool row_may_hit(const float4 &A, const float4 &B, const float4 &C, float a2,
+                                            float fl_x, float fl_y, float s) {
+  const float kp = C.x;
   const float dy = A.y + fl_y;
   const float dx = A.x + fl_x;
   const float y0 = fmaf(A.z, dx, A.w * dy);
   const float y1 = fmaf(B.x, dx, B.y * dy);
   const float y2 = fmaf(B.z, dx, fmaf(B.w, dy, 1.f));
-  float f = fmaf(kp, fmaf(y0, y0, y1 * y1), -y2 * y2);
-  float d = fmaf(2.f, fmaf(kp, fmaf(y0, A.z, y1 * B.x), -y2 * B.z), 0.5f * a2);
-  const float margin = 1e-3f + 1e-5f * (fabsf(f) + float(PX) * fabsf(d) + float(PX * PX) * fabsf(a2));
-  float m = f;
-#pragma unroll
-  for (int k = 1; k < PX; ++k) {
-    f += d;
-    d += a2;
-    m = fminf(m, f);
-  }
-  return !(m > margin);
+  const float q0 = fmaf(y0, y0, y1 * y1);
+  const float r0 = y2 * y2;
+  const float f0 = fmaf(kp, q0, -r0);
+  constexpr float L = float(PX - 1);
+  const float sL = s * L;
+  // df/dcolumn at the first pixel, scaled to the whole segment
+  const float G1 = 2.f * fmaf(kp, fmaf(y0, A.z, y1 * B.x), -y2 * B.z) * sL;
+  const float A2 = a2 * (sL * sL);
+  const float margin =
+      1e-3f + 1e-5f * (2.f * fmaf(kp, q0, r0) + 2.f * (sL * sL) * C.w + fabsf(G1) + fabsf(A2));
+  const float fe = f0 + G1 + 0.5f * A2;
+  const bool vertex_in = G1 < 0.f && G1 + A2 > 0.f;
+  return f0 <= margin || fe <= margin || (vertex_in && 2.f * A2 * (f0 - margin) <= G1 * G1);
 }
 
-// Support test of PX consecutive pixels (columns fl_x .. fl_x + PX - 1 of row fl_y,
-// relative to the tile origin).  Returns the hit mask; q, r (and y) per pixel.
+// Support test of PX pixels of one row (columns fl_x + k s, k = 0 .. PX-1, row fl_y,
+// relative to the tile origin; s a power of two).  Returns the hit mask; q, r (and y) per
+// pixel.
 template <int PX>
 __device__ __forceinline__ uint32_t eval_pixels(const float4 &A, const float4 &B, float kp, float fl_x, float fl_y,
-                                                float q[PX], float r[PX], float y0s[PX], float y1s[PX],
+                                                float s, float q[PX], float r[PX], float y0s[PX], float y1s[PX],
                                                 float y2s[PX]) {
   const float dy = A.y + fl_y;
   const float dx = A.x + fl_x;
   float y0 = fmaf(A.z, dx, A.w * dy);
   float y1 = fmaf(B.x, dx, B.y * dy);
   float y2 = fmaf(B.z, dx, fmaf(B.w, dy, 1.f));
+  const float st0 = s * A.z, st1 = s * B.x, st2 = s * B.z;
   uint32_t hit = 0;
 #pragma unroll
   for (int k = 0; k < PX; ++k) {
-    if (k) { y0 += A.z; y1 += B.x; y2 += B.z; }
+    if (k) { y0 += st0; y1 += st1; y2 += st2; }
     q[k] = fmaf(y0, y0, y1 * y1);
     r[k] = y2 * y2;
     y0s[k] = y0; y1s[k] = y1; y2s[k] = y2;

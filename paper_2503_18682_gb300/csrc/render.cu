@@ -10,8 +10,11 @@
 //   contributes iff y2 > 0 and kp q - r <= 0          (D <= kappa, Eq. support)
 //   D log2(e)/2 = c2h q / (q + r)                     (fragment formula)
 //   omega = min(alpha_max, 2^(log2 o - D log2(e)/2))
-// The PX pixels of a thread share the row term of y and step the column term by one
-// pixel (y += G[:,0]).  Compositing of a pixel stops before a primitive that would take T
+// A thread's PX pixels lie on one tile row, interleaved with the other threads of that
+// row (columns lx, lx + QX, lx + 2 QX, ...), so that a footprint covering a range of
+// columns hits the same pixel slots k in every lane of the row and the per-slot
+// compositing stays convergent.  The PX pixels share the row term of y and step the
+// column term by QX pixels (y += QX G[:,0]).  Compositing of a pixel stops before a primitive that would take T
 // below t_stop; a thread skips records once its pixels have all stopped, and the CTA
 // leaves the list once every thread has.
 #include "raygs_internal.cuh"
@@ -38,11 +41,11 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
   const int local = tile - cam.tile_base;
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
   const int px0 = tx * TW, py0 = ty * TH;
-  const int lx = (tid % QX) * PX, ly = tid / QX;
+  const int lx = tid % QX, ly = tid / QX;
   const int px = px0 + lx, py = py0 + ly;
   const uint2 rg = P.ranges[tile];
   const float ox_tile = float(px0) + 0.5f, oy_tile = float(py0) + 0.5f;
-  const float fl_x = float(lx), fl_y = float(ly);
+  const float fl_x = float(lx), fl_y = float(ly), step = float(QX);
 
   float T[PX], C0[PX], C1[PX], C2[PX];
   int last[PX];
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
 #pragma unroll
   for (int k = 0; k < PX; ++k) {
     T[k] = 1.f; C0[k] = 0.f; C1[k] = 0.f; C2[k] = 0.f; last[k] = 0;
-    if (py < cam.H && px + k < cam.W) alive |= 1u << k;
+    if (py < cam.H && px + k * QX < cam.W) alive |= 1u << k;
   }
   const uint32_t inside = alive;
   unsigned long long n_eval = 0, n_comp = 0;
@@ -70,14 +73,14 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
     const int nb = min(NB, int(rg.y - start));
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
-      const float kp = s_C[j].x;
+      const float4 Cc = s_C[j];
       if (COUNT) n_eval += __popc(alive);
-      if (!row_may_hit<PX>(A, B, kp, s_D[j].w, fl_x, fl_y)) continue;
+      // the instrumented variant tests every pixel, so its image checks the filter
+      if (!COUNT && !row_may_hit<PX>(A, B, Cc, s_D[j].w, fl_x, fl_y, step)) continue;
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
-      uint32_t hit = eval_pixels<PX>(A, B, kp, fl_x, fl_y, q, r, y0, y1, y2);
+      uint32_t hit = eval_pixels<PX>(A, B, Cc.x, fl_x, fl_y, step, q, r, y0, y1, y2);
       hit &= alive;
       if (hit) {
-        const float4 Cc = s_C[j];
         const float4 Dd = s_D[j];
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
@@ -105,11 +108,12 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
       if (inside & (1u << k)) {
-        P.rgb[3 * (pix + k)] = C0[k];
-        P.rgb[3 * (pix + k) + 1] = C1[k];
-        P.rgb[3 * (pix + k) + 2] = C2[k];
-        if (P.Tf) P.Tf[pix + k] = T[k];
-        if (P.ncontrib) P.ncontrib[pix + k] = last[k];
+        const long long o = pix + k * QX;
+        P.rgb[3 * o] = C0[k];
+        P.rgb[3 * o + 1] = C1[k];
+        P.rgb[3 * o + 2] = C2[k];
+        if (P.Tf) P.Tf[o] = T[k];
+        if (P.ncontrib) P.ncontrib[o] = last[k];
       }
     }
   }

@@ -184,3 +184,27 @@ def test_autotuner_picks_a_compiled_shape(oracle_lib):
     assert all(v > 0 for v in times.values()), times
     assert times[f"{kw['tile_w']}x{kw['tile_h']}"] == min(times.values())
     check_views(scene, cams, oracle_lib, tile_w=kw["tile_w"], tile_h=kw["tile_h"])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (32, 16), (8, 8)])
+def test_segment_filter_never_changes_a_pixel(tile):
+    """The rasteriser skips a thread's row segment when a conservative bound says no pixel
+    of it can pass the support test; the instrumented variant tests every pixel.  Both
+    images (rgb, T, last index) must be bit-identical, on large, small, MIP-filtered and
+    near-degenerate footprints."""
+    import torch
+    from paper_2503_18682_gb300 import raygs
+    scene = scenes.blob_scene(60000, seed=21, degenerate_frac=0.1)
+    R1, t1 = scenes.look_at([0.0, 0.0, 0.5], [0.0, 0.0, 6.0])
+    R2, t2 = scenes.look_at([2.5, 1.0, 3.0], [0.0, 0.0, 6.0])
+    cams = [scenes.make_camera(301, 197, 260.0, 260.0, R=R1, t=t1),
+            scenes.make_camera(256, 160, 500.0, 500.0, R=R2, t=t2),
+            scenes.make_camera(120, 90, 90.0, 90.0, R=R2, t=t2, mip=True)]
+    r = raygs.Renderer(cams, scene["means"].shape[0], tile_w=tile[0], tile_h=tile[1])
+    st = raygs.scene_to_device(scene)
+    rgb, T, nc = r.forward(st)
+    rgb2, T2, nc2 = r.alloc_outputs()
+    evals, comps = r.counted_render(rgb2, T2, nc2)
+    torch.cuda.synchronize()
+    assert 0 < comps <= evals
+    assert torch.equal(rgb, rgb2) and torch.equal(T, T2) and torch.equal(nc, nc2)
