@@ -6,6 +6,18 @@
 
 namespace raygs {
 
+// Asynchronous global -> shared copy of one 64-byte record (four 16-byte cp.async
+// transfers, bypassing L1), completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16 * c), "l"(g + 16 * c) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Staged record (shared-memory layout of one 64-byte Rec, tile-relative):
 //   A = (ox, oy, G00, G01)   ox, oy: tile origin pixel centre minus projected centre
 //   B = (G10, G11, h0, h1)

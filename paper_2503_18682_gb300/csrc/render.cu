@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
   constexpr int NB = 2 * NT;        // records per batch
   constexpr int QX = TW / PX;       // threads per tile row
   __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
+  __shared__ Rec s_raw[NB];
   __shared__ int s_view;
   const int tile = blockIdx.x;
   const int tid = threadIdx.x;
@@ -58,18 +59,44 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
   const uint32_t inside = alive;
   unsigned long long n_eval = 0, n_comp = 0;
 
+  // Records move through a two-stage pipeline: while a batch is composited, the raw
+  // records of the next batch are in flight to shared memory (cp.async) and the record
+  // indices of the batch after that are being loaded into registers.
+  constexpr int PER = NB / NT;
+  uint32_t nxt[PER];
+#pragma unroll
+  for (int rr = 0; rr < PER; ++rr) {
+    const uint32_t i = rg.x + tid + rr * NT;
+    if (i < rg.y) cp_async_rec(&s_raw[tid + rr * NT], &P.rec[P.pairs[P.inst_vals[i]]]);
+  }
+  cp_async_commit();
+#pragma unroll
+  for (int rr = 0; rr < PER; ++rr) {
+    const uint32_t i = rg.x + NB + tid + rr * NT;
+    nxt[rr] = i < rg.y ? P.pairs[P.inst_vals[i]] : 0u;
+  }
+
   for (uint32_t start = rg.x; start < rg.y; start += NB) {
     if (__syncthreads_and(alive == 0)) break;
+    cp_async_wait_all();  // this thread's raw slots of the batch have landed
 #pragma unroll
-    for (int rr = 0; rr < NB / NT; ++rr) {
+    for (int rr = 0; rr < PER; ++rr) {
       const int slot = tid + rr * NT;
-      const uint32_t i = start + slot;
-      if (i < rg.y) {
-        const Rec r = P.rec[P.pairs[P.inst_vals[i]]];
-        stage_record(r, ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
-      }
+      if (start + slot < rg.y)
+        stage_record(s_raw[slot], ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
     }
     __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < PER; ++rr) {
+      const uint32_t i = start + NB + tid + rr * NT;
+      if (i < rg.y) cp_async_rec(&s_raw[tid + rr * NT], &P.rec[nxt[rr]]);
+    }
+    cp_async_commit();
+#pragma unroll
+    for (int rr = 0; rr < PER; ++rr) {
+      const uint32_t i = start + 2 * NB + tid + rr * NT;
+      nxt[rr] = i < rg.y ? P.pairs[P.inst_vals[i]] : 0u;
+    }
     const int nb = min(NB, int(rg.y - start));
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
@@ -103,6 +130,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
       }
     }
   }
+  cp_async_wait_all();  // no copy may outlive the block
   if (inside) {
     const long long pix = cam.pix_base + (long long)py * cam.W + px;
 #pragma unroll
