@@ -405,6 +405,63 @@ __device__ __forceinline__ bool ellipse_band(const Ell &e, float ya, float yb, f
   return true;
 }
 
+// Supports that are not a bounded ellipse (the primitive's cone of rays reaches the
+// camera plane, or the ellipse is too ill-conditioned in float32) are still convex: the
+// image of one nappe of an elliptic cone cut by the plane z = 1.  Within a band of pixel
+// rows their pixels therefore occupy one contiguous run of tiles, found by testing tile
+// rectangles from both ends of the row.
+
+// Does the segment delta(t) = P + t E, t in [0, 1] (pixel offsets from the projected
+// centre) meet the support kp |G delta|^2 <= y2^2, y2 = 1 + h.delta > 0?  Along the
+// segment y01 = a + t b and y2 = al + t be, so f = kp |y01|^2 - y2^2 is a quadratic in t;
+// its minimum over the part where y2 > 0 is compared with a margin of 1e-4 of the
+// magnitude of its terms, far above float32 rounding: the answer errs only towards yes.
+__device__ __forceinline__ bool segment_meets_support(const Rec &r, float Px, float Py, float Ex, float Ey) {
+  const float kp = r.c.z;
+  const float a0 = fmaf(r.b.x, Px, r.b.y * Py), a1 = fmaf(r.b.z, Px, r.b.w * Py);
+  const float b0 = fmaf(r.b.x, Ex, r.b.y * Ey), b1 = fmaf(r.b.z, Ex, r.b.w * Ey);
+  const float al = fmaf(r.c.x, Px, fmaf(r.c.y, Py, 1.f)), be = fmaf(r.c.x, Ex, r.c.y * Ey);
+  const float slack = 1e-5f * (fabsf(al) + fabsf(be)) + 1e-6f;
+  float t0 = 0.f, t1 = 1.f;
+  if (be > 0.f) t0 = fmaxf(t0, (-slack - al) / be);
+  else if (be < 0.f) t1 = fminf(t1, (-slack - al) / be);
+  else if (al < -slack) return false;
+  if (!(t0 <= t1)) return false;
+  const float qa = fmaf(a0, a0, a1 * a1), qb = fmaf(b0, b0, b1 * b1), qab = fmaf(a0, b0, a1 * b1);
+  const float A = fmaf(kp, qb, -be * be);
+  const float Bh = fmaf(kp, qab, -al * be);
+  const float Cc = fmaf(kp, qa, -al * al);
+  const float margin = 1e-4f * (2.f * fmaf(kp, qa, al * al) + 2.f * fmaf(kp, qb, be * be)) + 1e-6f;
+  float m = fminf(fmaf(fmaf(A, t0, 2.f * Bh), t0, Cc), fmaf(fmaf(A, t1, 2.f * Bh), t1, Cc));
+  if (A > 0.f) {
+    const float tv = -Bh / A;
+    if (tv > t0 && tv < t1) m = fminf(m, fmaf(Bh, tv, Cc));
+  }
+  return m <= margin;
+}
+
+// First (from_left) or last tile column in [tx0, tx1] whose pixel centres in rows
+// [ya, yb] can meet the support; -1 if none.
+__device__ int support_tile_end(const Rec &r, const DevCam &cam, int tile_w, float ya, float yb, int tx0, int tx1,
+                                bool from_left) {
+  const float ux = r.a.x, uy = r.a.y, lx = r.a.z, ly = r.a.w;
+  const float dya = (ya - uy) - ly, dyb = (yb - uy) - ly;
+  const int n = tx1 - tx0 + 1;
+  for (int i = 0; i < n; ++i) {
+    const int tx = from_left ? tx0 + i : tx1 - i;
+    const float xa = float(tx * tile_w) + 0.5f;
+    const float xb = float(min((tx + 1) * tile_w, cam.W)) - 0.5f;
+    const float dxa = (xa - ux) - lx, dxb = (xb - ux) - lx;
+    if ((dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) ||      // the centre itself
+        segment_meets_support(r, dxa, dya, 0.f, dyb - dya) ||
+        segment_meets_support(r, dxb, dya, 0.f, dyb - dya) ||
+        segment_meets_support(r, dxa, dya, dxb - dxa, 0.f) ||
+        segment_meets_support(r, dxa, dyb, dxb - dxa, 0.f))
+      return tx;
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   __shared__ uint32_t s_off[kEmitTile + 1];
   __shared__ uint32_t s_pair[kEmitTile + 1];
@@ -436,10 +493,19 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
       uint32_t xa_t = tx0, xb_t = tx1;
       const Ell el = R.ell[pair];
       bool empty = false;
-      if (el.rho >= 0.f) {
-        const DevCam &cam = R.cams[pair / uint32_t(R.n)];
-        const float ya = float(ty * R.tile_h) + 0.5f;
-        const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
+      const DevCam &cam = R.cams[pair / uint32_t(R.n)];
+      const float ya = float(ty * R.tile_h) + 0.5f;
+      const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
+      if (el.rho < 0.f) {
+        const Rec rc = R.rec[pair];
+        const int a0 = support_tile_end(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), true);
+        if (a0 < 0) {
+          empty = true;
+        } else {
+          xa_t = uint32_t(a0);
+          xb_t = uint32_t(support_tile_end(rc, cam, R.tile_w, ya, yb, a0, int(tx1), false));
+        }
+      } else {
         float xa, xb;
         if (!ellipse_band(el, ya - 0.02f, yb + 0.02f, xa, xb)) {
           empty = true;

@@ -187,6 +187,7 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   R.pairs = pairs;
   R.rect = w.at<uint2>(w.L.rect);
   R.ell = w.at<Ell>(w.L.ell);
+  R.rec = w.at<Rec>(w.L.rec);
   R.row_off = J.off;
   R.row_tstart = J.tile_start;
   R.cams = w.at<DevCam>(w.L.cams);

@@ -197,6 +197,7 @@ struct RowsParams {
   const uint32_t *pairs;    // sorted pair ids
   const uint2 *rect;
   const Ell *ell;
+  const Rec *rec;
   const uint32_t *row_off;
   const uint32_t *row_tstart;
   const DevCam *cams;

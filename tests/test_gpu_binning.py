@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2503_18682_gb300 import scenes
-from tests.gpu_util import gpu_render
+from tests.gpu_util import assert_parity, compare, gpu_render, sample_pixels, view_slice
 
 pytestmark = pytest.mark.gpu
 
@@ -118,6 +118,79 @@ def test_sort_and_tile_lists(oracle_lib, tile):
         k = kv != CULLED
         np.testing.assert_array_equal(kv[k], info[k, 1].astype(np.uint32))
         assert np.all(info[k, 0] == 0)
+
+
+def assert_dropped_tiles_miss_support(oracle_lib, scene, cams, r, n, tile, pairs_to_check):
+    """Every tile of a pair's rectangle that the binning dropped holds no pixel centre of the
+    pair's support (FP64 oracle, brute force).  Returns (dropped tiles checked, rectangle
+    tiles, kept instances) over the checked pairs."""
+    tw, th = tile
+    rects = fetch(r.debug_buffer(1), 2 * n * len(cams), np.uint32).reshape(-1, 2)
+    ctr = r.last_counters
+    order = fetch(r.debug_buffer(3), ctr["n_visible"], np.uint32)
+    ni = ctr["n_instances"]
+    g_tiles = fetch(r.debug_buffer(4), ni, np.uint32).astype(np.int64)
+    g_pos = fetch(r.debug_buffer(5), ni, np.uint32).astype(np.int64)
+    kept = {}
+    for t, p in zip(g_tiles, g_pos):
+        kept.setdefault(int(p), set()).add(int(t))
+    infos = [oracle_lib.prepare(scene, cam) for cam in cams]
+    dropped = n_rect = n_kept = 0
+    for p, pair in enumerate(order):
+        if int(pair) not in pairs_to_check:
+            continue
+        v, g = divmod(int(pair), n)
+        x0, y0, x1, y1 = rect_of(rects, pair)
+        base = tile_base_of(r, v)
+        tx_n = -(-cams[v]["width"] // tw)
+        rect_tiles = {base + ty * tx_n + tx for ty in range(y0, y1 + 1) for tx in range(x0, x1 + 1)}
+        mine = kept.get(p, set())
+        assert mine <= rect_tiles, (p, pair)
+        n_rect += len(rect_tiles)
+        n_kept += len(mine)
+        info = infos[v][g]
+        Si = info[14:23].reshape(3, 3) @ np.diag(info[11:14] ** -2.0) @ info[14:23].reshape(3, 3).T
+        cam = cams[v]
+        for t in rect_tiles - mine:
+            ty, tx = divmod(t - base, tx_n)
+            for py in range(ty * th, min(ty * th + th, cam["height"])):
+                for px in range(tx * tw, min(tx * tw + tw, cam["width"])):
+                    x = [(px + 0.5 - float(cam["cx"])) / float(cam["fx"]),
+                         (py + 0.5 - float(cam["cy"])) / float(cam["fy"]), 1.0]
+                    D, tau = oracle_lib.D_ray(info[2:5], Si, x)
+                    assert not (tau > 0 and D <= info[6]), (pair, t, px, py)
+            dropped += 1
+    return dropped, n_rect, n_kept
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16)])
+def test_unbounded_supports_keep_every_covered_tile(oracle_lib, tile):
+    """Large primitives near the camera whose support is not a bounded ellipse in the image
+    (their cone of rays reaches the camera plane): binning scans each tile row from both
+    ends for the first and last tile whose pixel centres can meet the support.  Every
+    dropped tile misses the support (oracle brute force), the scan drops tiles, and the
+    image keeps oracle parity."""
+    rng = np.random.default_rng(31)
+    n = 400
+    sc = scenes.uniform_scene(n, seed=31)
+    sc["means"] = np.concatenate([
+        rng.uniform([-0.4, -0.4, 0.03], [0.4, 0.4, 0.3], (n // 2, 3)),
+        rng.uniform([-1, -1, 0.3], [1, 1, 2.0], (n - n // 2, 3))]).astype(np.float32)
+    sc["log_scales"] = rng.uniform(np.log(0.03), np.log(0.5), (n, 3)).astype(np.float32)
+    R1, t1 = scenes.look_at([0.2, -0.1, -0.2], [0.0, 0.0, 1.0])
+    cams = [scenes.make_camera(96, 80, 70.0, 70.0), scenes.make_camera(120, 64, 60.0, 60.0, R=R1, t=t1)]
+    r, _, rgb, T, nc = gpu_render(sc, cams, tile_w=tile[0], tile_h=tile[1])
+    ell = fetch(r.debug_buffer(7), 8 * n * len(cams), np.float32).reshape(-1, 8)
+    order = fetch(r.debug_buffer(3), r.last_counters["n_visible"], np.uint32)
+    unbounded = {int(p) for p in order if ell[p, 5] < 0}
+    assert len(unbounded) >= 10, len(unbounded)
+    dropped, n_rect, n_kept = assert_dropped_tiles_miss_support(oracle_lib, sc, cams, r, n, tile, unbounded)
+    assert dropped > 0 and n_kept < n_rect
+    for v, cam in enumerate(cams):
+        sl = view_slice(r, v)
+        pix, idx = sample_pixels(cam, 1000, seed=v)
+        orc = oracle_lib.render(sc, cam, pixels=pix)
+        assert_parity(compare(rgb[sl][idx], T[sl][idx], orc))
 
 
 def test_rects_match_oracle_quad(oracle_lib):
