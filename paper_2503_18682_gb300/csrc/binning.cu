@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(1024) scan_single_cta(uint32_t *data, int n, u
 }
 
 template <int BITS>
-__global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
+__global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
   constexpr int R = 1 << BITS;
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
@@ -154,18 +154,33 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
 
+  // keys and values of the next tile are loaded while the current one is ranked
+  uint32_t nkey[kSortIPT], nval[kSortIPT];
+  auto load_tile = [&](uint32_t base) {
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
+      const bool ok = idx < hi;
+      nkey[r] = ok ? p.keys_in[idx] : 0u;
+      nval[r] = ok ? (p.filter ? idx : p.vals_in[idx]) : 0u;
+    }
+  };
+  if (lo < hi) load_tile(lo);
   for (uint32_t base = lo; base < hi; base += kSortTile) {
     for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
-    __syncthreads();
     uint32_t key[kSortIPT], val[kSortIPT], off[kSortIPT];
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) { key[r] = nkey[r]; val[r] = nval[r]; }
+    if (base + kSortTile < hi) load_tile(base + kSortTile);
+    __syncthreads();
     uint32_t vmask = 0;
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
-      uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
-      bool ok = idx < hi;
-      uint32_t k = ok ? p.keys_in[idx] : 0u;
-      uint32_t v = ok ? (p.filter ? idx : p.vals_in[idx]) : 0u;
-      bool valid = ok && !(p.filter && k == kCulled);
+      const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
+      const bool ok = idx < hi;
+      const uint32_t k = key[r];
+      const uint32_t v = val[r];
+      const bool valid = ok && !(p.filter && k == kCulled);
       uint32_t d = (k >> p.shift) & (R - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
       uint32_t c = valid ? s_cnt[warp][d] : 0u;
@@ -173,8 +188,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep(SortPass p) {
       if (valid && lane == 31 - __clz(peers)) s_cnt[warp][d] = c + __popc(peers);
       __syncwarp();
       off[r] = c + __popc(peers & lt);
-      key[r] = k;
-      val[r] = v;
       vmask |= valid ? (1u << r) : 0u;
     }
     __syncthreads();
