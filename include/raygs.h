@@ -99,6 +99,9 @@ typedef struct {
   int64_t capacity;     /* instance capacity of the plan */
   int64_t n_nonfinite;  /* primitives culled because an attribute was NaN/Inf */
   int32_t overflow;     /* 1 when n_instances > capacity: the image is incomplete */
+  int32_t pad;
+  int64_t n_rows;       /* (pair, tile row) support rows, including empty ones */
+  int64_t n_rows_kept;  /* support rows that hold at least one tile */
 } raygs_counters;
 
 /* Reference-gradient outputs of raygs_render_backward: float32 device buffers laid out

@@ -74,15 +74,9 @@ raygs_status raygs_plan_create(const raygs_camera *cams, int32_t n_views, int64_
   if (!p) return RAYGS_ERR_INVALID_ARG;
   p->cams.assign(cams, cams + n_views);
   p->dcams.resize(n_views);
-  int64_t tb = 0, pb = 0;
-  for (int v = 0; v < n_views; ++v) {
-    fill_devcam(cams[v], cfg, p->dcams[v]);
-    p->dcams[v].tile_base = int(tb);
-    p->dcams[v].pix_base = pb;
-    tb += int64_t(p->dcams[v].tiles_x) * p->dcams[v].tiles_y;
-    pb += int64_t(cams[v].width) * cams[v].height;
-  }
-  if (tb >= (int64_t(1) << 31)) {
+  int64_t tb = 0, trows = 0, pb = 0;
+  int max_tx = 0;
+  if (!plan_views(cams, n_views, cfg, p->dcams.data(), tb, trows, pb, max_tx)) {
     delete p;
     return RAYGS_ERR_INVALID_ARG;
   }
@@ -94,11 +88,13 @@ raygs_status raygs_plan_create(const raygs_camera *cams, int32_t n_views, int64_
   w.n_views = n_views;
   w.n = n_gaussians;
   w.tiles = tb;
+  w.trows = trows;
+  w.max_tiles_x = max_tx;
   w.cap = max_instances;
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  w.L = make_layout(n_views, n_gaussians, tb, max_instances, w.G, cfg.enable_backward != 0);
+  w.L = make_layout(n_views, n_gaussians, tb, trows, max_instances, w.G, cfg.enable_backward != 0);
   p->total_pixels = pb;
   *out = p;
   return RAYGS_OK;
@@ -138,6 +134,7 @@ raygs_status raygs_plan_set_poses(raygs_plan *plan, const raygs_camera *cams, vo
     DevCam d;
     fill_devcam(cams[v], plan->w.cfg, d);
     d.tile_base = plan->dcams[v].tile_base;
+    d.trow_base = plan->dcams[v].trow_base;
     d.pix_base = plan->dcams[v].pix_base;
     plan->dcams[v] = d;
     plan->cams[v] = cams[v];
@@ -204,6 +201,9 @@ raygs_status raygs_read_counters(raygs_plan *plan, raygs_counters *out, void *st
   out->capacity = plan->w.cap;
   out->n_nonfinite = int64_t(h.n_nonfinite);
   out->overflow = int32_t(h.overflow);
+  out->pad = 0;
+  out->n_rows = int64_t(h.n_rows);
+  out->n_rows_kept = int64_t(h.n_rows_kept);
   return RAYGS_OK;
 }
 
@@ -276,8 +276,9 @@ raygs_status raygs_debug_render_counted(raygs_plan *plan, float *rgb, float *T_f
 
 /* Device pointers of internal buffers (valid after bin_sort):
  * which: 0 depth keys [V*N], 1 rects [V*N] (uint2), 2 records [V*N] (64 B),
- *        3 sorted pair ids [n_visible], 4 instance tile ids [n_instances] (sorted),
- *        5 instance sorted-pair positions, 6 tile ranges [tiles] (uint2),
+ *        3 sorted pair ids [n_visible], 4 support rows sorted by tile row [n_rows_kept]
+ *        (uint2: sorted pair position, first tile column | run length << 16),
+ *        5 instance lists (sorted pair positions, tile by tile), 6 tile ranges [tiles] (uint2),
  *        7 support ellipses [V*N] (32 B), 8 raw counters */
 void *raygs_debug_buffer(raygs_plan *plan, int which) {
   if (!plan || !plan->w.base) return nullptr;
@@ -287,8 +288,8 @@ void *raygs_debug_buffer(raygs_plan *plan, int which) {
     case 1: return w.base + w.L.rect;
     case 2: return w.base + w.L.rec;
     case 3: return w.base + w.L.s1v[w.s1_final];
-    case 4: return w.base + w.L.ik[w.s2_final];
-    case 5: return w.base + w.L.iv[w.s2_final];
+    case 4: return w.base + w.L.rv[w.s2_rows];
+    case 5: return w.base + w.L.inst;
     case 6: return w.base + w.L.ranges;
     case 7: return w.base + w.L.ell;
     case 8: return w.base + w.L.counters;

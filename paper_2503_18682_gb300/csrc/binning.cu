@@ -137,11 +137,30 @@ __global__ void __launch_bounds__(1024) scan_single_cta(uint32_t *data, int n, u
   if (d_total && threadIdx.x == 0) *d_total = tot;
 }
 
-template <int BITS>
+// Values are 4-byte item ids, or (WIDE) the 8-byte payload of a support row.
+template <bool WIDE>
+struct SortVal {
+  using T = uint32_t;
+  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) { return p.filter ? idx : p.vals_in[idx]; }
+  static __device__ __forceinline__ void store(const SortPass &p, uint32_t dst, T v) { p.vals_out[dst] = v; }
+};
+template <>
+struct SortVal<true> {
+  using T = uint2;
+  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) {
+    if (!p.filter) return p.wvals_in[idx];
+    const uint2 sg = p.seg[idx];
+    return make_uint2(sg.x, (sg.y >> 16) | (p.seg_len[idx] << 16));
+  }
+  static __device__ __forceinline__ void store(const SortPass &p, uint32_t dst, T v) { p.wvals_out[dst] = v; }
+};
+
+template <int BITS, bool WIDE>
 __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
   constexpr int R = 1 << BITS;
+  using VT = typename SortVal<WIDE>::T;
   __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ VT s_vals[kSortTile];
   __shared__ uint32_t s_cnt[kSortWarps][R];
   __shared__ uint32_t s_base[R];
   __shared__ uint32_t s_tpre[R];
@@ -155,23 +174,28 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
   const uint32_t lt = (1u << lane) - 1u;
 
   // keys and values of the next tile are loaded while the current one is ranked
-  uint32_t nkey[kSortIPT], nval[kSortIPT];
+  uint32_t nkey[kSortIPT];
+  VT nval[kSortIPT];
   auto load_tile = [&](uint32_t base) {
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
       const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
       const bool ok = idx < hi;
       nkey[r] = ok ? p.keys_in[idx] : 0u;
-      nval[r] = ok ? (p.filter ? idx : p.vals_in[idx]) : 0u;
+      nval[r] = ok ? SortVal<WIDE>::load(p, idx) : VT{};
     }
   };
-  if (lo < hi) load_tile(lo);
+  // (the 8-byte values would not leave registers for the prefetch)
+  constexpr bool kPrefetch = !WIDE;
+  if (kPrefetch && lo < hi) load_tile(lo);
   for (uint32_t base = lo; base < hi; base += kSortTile) {
     for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
-    uint32_t key[kSortIPT], val[kSortIPT], off[kSortIPT];
+    uint32_t key[kSortIPT], off[kSortIPT];
+    VT val[kSortIPT];
+    if (!kPrefetch) load_tile(base);
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) { key[r] = nkey[r]; val[r] = nval[r]; }
-    if (base + kSortTile < hi) load_tile(base + kSortTile);
+    if (kPrefetch && base + kSortTile < hi) load_tile(base + kSortTile);
     __syncthreads();
     uint32_t vmask = 0;
 #pragma unroll
@@ -179,7 +203,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
       const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
       const bool ok = idx < hi;
       const uint32_t k = key[r];
-      const uint32_t v = val[r];
       const bool valid = ok && !(p.filter && k == kCulled);
       uint32_t d = (k >> p.shift) & (R - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
@@ -238,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
       uint32_t d = (k >> p.shift) & (R - 1);
       uint32_t dst = s_base[d] + j - s_tpre[d];
       p.keys_out[dst] = k;
-      p.vals_out[dst] = s_vals[j];
+      SortVal<WIDE>::store(p, dst, s_vals[j]);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < R; d += kSortThreads) s_base[d] += s_tot[d];
@@ -306,8 +329,9 @@ cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
   hist_reduce_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
   hist_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nb, p.d_total);
   hist_offsets_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
-  if (p.bits == 9) sort_downsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
-  else sort_downsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  if (p.wide) sort_downsweep<8, true><<<p.G, kSortThreads, 0, st>>>(p);
+  else if (p.bits == 9) sort_downsweep<9, false><<<p.G, kSortThreads, 0, st>>>(p);
+  else sort_downsweep<8, false><<<p.G, kSortThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -324,7 +348,7 @@ __device__ __forceinline__ void cta_range_units(uint32_t count, uint32_t &lo, ui
 __global__ void __launch_bounds__(256) scan_reduce_kernel(ScanJob J) {
   __shared__ uint32_t ws[33];
   uint32_t lo, hi;
-  cta_range_units(*J.d_n, lo, hi);
+  cta_range_units(J.d_n ? *J.d_n : J.n_static, lo, hi);
   uint32_t s = 0;
   for (uint32_t p = lo + threadIdx.x; p < hi; p += blockDim.x) s += J.cnt[p];
   uint32_t tot;
@@ -350,7 +374,7 @@ __global__ void __launch_bounds__(32) scan_partials_kernel(ScanJob J, int G) {
 __global__ void __launch_bounds__(256) scan_offsets_kernel(ScanJob J) {
   __shared__ uint32_t ws[33];
   uint32_t lo, hi;
-  cta_range_units(*J.d_n, lo, hi);
+  cta_range_units(J.d_n ? *J.d_n : J.n_static, lo, hi);
   uint32_t carry = J.partial[blockIdx.x];
   for (uint32_t base = lo; base < hi; base += 256 * 4) {
     uint32_t c[4], s = 0;
@@ -538,6 +562,7 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
       }
       R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
       R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
+      R.row_key[e] = empty ? kCulled : uint32_t(cam.trow_base) + ty;
     }
     __syncthreads();
   }
@@ -548,55 +573,9 @@ cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------- emission
-__global__ void __launch_bounds__(256) emit_kernel(EmitParams E) {
-  __shared__ uint32_t s_off[kEmitTile + 1];
-  __shared__ uint2 s_seg[kEmitTile + 1];
-  const uint32_t total = E.counters->n_inst_clamped;
-  const unsigned long long total_all = E.counters->n_instances;
-  const uint32_t nrows = E.counters->n_rows_clamped;
-  const uint32_t ntile = (total + kEmitTile - 1) / kEmitTile;
-  const unsigned long long ntile_all = (total_all + kEmitTile - 1) / kEmitTile;
-  for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
-    const uint32_t e0 = t * kEmitTile, e1 = min(e0 + uint32_t(kEmitTile), total);
-    const uint32_t r_lo = E.tile_start[t];
-    const uint32_t r_hi = (uint64_t(t) + 1 < ntile_all) ? E.tile_start[t + 1] : nrows - 1;
-    const int nr = int(r_hi - r_lo) + 1;
-    const bool in_smem = nr <= kEmitTile + 1;  // rows of zero length can make it larger
-    if (in_smem) {
-      for (int j = threadIdx.x; j < nr; j += blockDim.x) {
-        s_off[j] = E.seg_off[r_lo + j];
-        s_seg[j] = E.seg[r_lo + j];
-      }
-    }
-    __syncthreads();
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      int a = 0, b = nr - 1;  // largest row with offset <= e (a row of length 0 never wins)
-      while (a < b) {
-        int m = (a + b + 1) >> 1;
-        uint32_t om = in_smem ? s_off[m] : E.seg_off[r_lo + m];
-        if (om <= e) a = m; else b = m - 1;
-      }
-      const uint2 sg = in_smem ? s_seg[a] : E.seg[r_lo + a];
-      const uint32_t off = in_smem ? s_off[a] : E.seg_off[r_lo + a];
-      const uint32_t pos = sg.x;
-      const uint32_t ty = sg.y & 0xFFFF, tx = (sg.y >> 16) + (e - off);
-      const DevCam &cam = E.cams[E.pairs[pos] / uint32_t(E.n)];
-      E.keys[e] = uint32_t(cam.tile_base) + ty * uint32_t(cam.tiles_x) + tx;
-      E.vals[e] = pos;
-    }
-    __syncthreads();
-  }
-}
-
-cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st) {
-  emit_kernel<<<G, 256, 0, st>>>(E);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------- tile ranges
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const Counters *c, uint2 *ranges) {
-  const uint32_t n = c->n_inst_clamped;
+__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges) {
+  const uint32_t n = *d_n;
   const uint32_t nq = (n + 3) / 4;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
     const uint32_t i0 = 4 * q;
@@ -623,9 +602,160 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const
   }
 }
 
-cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st) {
-  ranges_kernel<<<G, 256, 0, st>>>(keys, c, ranges);
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st) {
+  ranges_kernel<<<G, 256, 0, st>>>(keys, d_n, ranges);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------- tile rows -> per-tile instance lists
+__device__ __forceinline__ const DevCam &view_of_trow(const ExpandParams &E, int grow, int &v_out) {
+  int v = 0;
+  while (v + 1 < E.n_views && E.cams[v + 1].trow_base <= grow) ++v;
+  v_out = v;
+  return E.cams[v];
+}
+
+// Instances per tile of one tile row: each sorted row covers the tile columns
+// [txa, txa + len); a difference array over the columns and its prefix sum count them.
+__global__ void __launch_bounds__(256) tile_count_kernel(ExpandParams E) {
+  extern __shared__ uint32_t s_diff[];  // [tiles_x + 1]
+  __shared__ uint32_t s_ws[33];
+  __shared__ int s_v;
+  const int grow = blockIdx.x;
+  if (threadIdx.x == 0) { int v; view_of_trow(E, grow, v); s_v = v; }
+  __syncthreads();
+  const DevCam &cam = E.cams[s_v];
+  const int TX = cam.tiles_x;
+  for (int x = threadIdx.x; x <= TX; x += blockDim.x) s_diff[x] = 0;
+  __syncthreads();
+  const uint2 rr = E.trow_ranges[grow];
+  for (uint32_t i = rr.x + threadIdx.x; i < rr.y; i += blockDim.x) {
+    const uint32_t pk = E.rows[i].y;
+    const uint32_t xa = pk & 0xFFFFu, len = pk >> 16;
+    atomicAdd(&s_diff[xa], 1u);
+    atomicSub(&s_diff[xa + len], 1u);
+  }
+  __syncthreads();
+  // inclusive prefix of the differences = instances of each tile
+  const int per = (TX + int(blockDim.x) - 1) / int(blockDim.x);
+  const int x0 = min(TX, int(threadIdx.x) * per), x1 = min(TX, x0 + per);
+  uint32_t s = 0;
+  for (int x = x0; x < x1; ++x) s += s_diff[x];
+  uint32_t tot;
+  uint32_t run = block_excl_scan(s, s_ws, &tot);
+  const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
+  for (int x = x0; x < x1; ++x) {
+    run += s_diff[x];
+    E.tile_cnt[tile0 + x] = run;
+  }
+}
+
+// Instance lists of one tile row.  Rows are taken in sorted (depth) order, NT * KR at a
+// time, in 32-row groups (KR * NT / 32 groups: row q of the step is lane q % 32 of group
+// q / 32); every lane marks the tiles of its row in its group's bit mask per tile, and the
+// rank of (row, tile) is the tile's running cursor plus the rows of lower groups and lower
+// lanes that cover the same tile.  Each tile's list keeps depth order.  The masks are
+// double-buffered (the buffer of the next step is cleared while this one is read) and the
+// rows of the next step are loaded during this one.
+template <int NT, int KR>
+__global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
+  constexpr int VW = NT / 32 * KR;  // row groups per step
+  extern __shared__ uint32_t s_mem[];
+  __shared__ int s_v;
+  const int grow = blockIdx.x;
+  if (threadIdx.x == 0) { int v; view_of_trow(E, grow, v); s_v = v; }
+  __syncthreads();
+  const DevCam &cam = E.cams[s_v];
+  const int TX = cam.tiles_x;
+  uint32_t *s_cur = s_mem;                   // [TX] next free slot of each tile
+  uint32_t *s_pre = s_cur + TX;              // [VW][TX] first slot of each group
+  uint32_t *s_mask = s_pre + VW * TX;        // [2][VW][TX]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
+  for (int x = threadIdx.x; x < TX; x += NT) {
+    const uint32_t o = E.tile_off[tile0 + x], c = E.tile_cnt[tile0 + x];
+    s_cur[x] = o;
+    E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + c, E.cap));
+  }
+  for (int j = threadIdx.x; j < 2 * VW * TX; j += NT) s_mask[j] = 0u;
+  const uint2 rr = E.trow_ranges[grow];
+  constexpr uint32_t STEP = uint32_t(NT) * KR;
+  uint2 nxt[KR];
+  auto load_rows = [&](uint32_t base) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const uint32_t i = base + uint32_t(k * NT) + threadIdx.x;
+      nxt[k] = i < rr.y ? E.rows[i] : make_uint2(0u, 0u);
+    }
+  };
+  if (rr.x < rr.y) load_rows(rr.x);
+  int buf = 0;
+  for (uint32_t base = rr.x; base < rr.y; base += STEP) {
+    uint2 cur[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) cur[k] = nxt[k];
+    if (base + STEP < rr.y) load_rows(base + STEP);
+    uint32_t *mask = s_mask + buf * VW * TX;
+    __syncthreads();  // masks of this buffer cleared; the previous step's reads are done
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int g = k * (NT / 32) + warp;
+      const uint32_t xa = cur[k].y & 0xFFFFu, len = cur[k].y >> 16;
+      for (uint32_t t = 0; t < len; ++t) atomicOr(&mask[g * TX + int(xa + t)], 1u << lane);
+    }
+    __syncthreads();
+    uint32_t *other = s_mask + (1 - buf) * VW * TX;
+    for (int x = threadIdx.x; x < TX; x += NT) {
+      uint32_t run = s_cur[x];
+#pragma unroll 4
+      for (int g = 0; g < VW; ++g) {
+        s_pre[g * TX + x] = run;
+        run += __popc(mask[g * TX + x]);
+        other[g * TX + x] = 0u;
+      }
+      s_cur[x] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const int g = k * (NT / 32) + warp;
+      const uint32_t xa = cur[k].y & 0xFFFFu, len = cur[k].y >> 16;
+      for (uint32_t t = 0; t < len; ++t) {
+        const int x = int(xa + t);
+        const uint32_t dst = s_pre[g * TX + x] + __popc(mask[g * TX + x] & lt);
+        if (dst < E.cap) E.inst[dst] = cur[k].x;
+      }
+    }
+    buf = 1 - buf;
+  }
+}
+
+template <int NT, int KR>
+size_t expand_smem(int max_tiles_x) {
+  return sizeof(uint32_t) * size_t(max_tiles_x) * size_t(1 + 3 * (NT / 32) * KR);
+}
+
+cudaError_t launch_tile_counts(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {
+  if (n_trows == 0) return cudaSuccess;
+  tile_count_kernel<<<n_trows, 256, sizeof(uint32_t) * size_t(max_tiles_x + 1), st>>>(E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {
+  if (n_trows == 0) return cudaSuccess;
+  constexpr size_t kBudget = 200 * 1024;
+  auto run = [&](auto kernel, int nt, size_t smem) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+    }
+    kernel<<<n_trows, nt, smem, st>>>(E);
+    return cudaGetLastError();
+  };
+  if (expand_smem<256, 4>(max_tiles_x) <= kBudget) return run(expand_kernel<256, 4>, 256, expand_smem<256, 4>(max_tiles_x));
+  if (expand_smem<256, 1>(max_tiles_x) <= kBudget) return run(expand_kernel<256, 1>, 256, expand_smem<256, 1>(max_tiles_x));
+  return run(expand_kernel<128, 1>, 128, expand_smem<128, 1>(max_tiles_x));
 }
 
 }  // namespace raygs

@@ -65,15 +65,9 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
 
   // Per-view constants, on the stack (no heap).
   DevCam dc[RAYGS_MAX_VIEWS];
-  int64_t tiles = 0, pixels = 0;
-  for (int v = 0; v < n_views; ++v) {
-    if (!camera_valid(cams[v])) return RAYGS_ERR_INVALID_ARG;
-    fill_devcam(cams[v], cfg, dc[v]);
-    dc[v].tile_base = int(tiles);
-    dc[v].pix_base = pixels;
-    tiles += int64_t(dc[v].tiles_x) * dc[v].tiles_y;
-    pixels += int64_t(cams[v].width) * cams[v].height;
-  }
+  int64_t tiles = 0, trows = 0, pixels = 0;
+  int max_tx = 0;
+  if (!plan_views(cams, n_views, cfg, dc, tiles, trows, pixels, max_tx)) return RAYGS_ERR_INVALID_ARG;
 
   void *scratch = nullptr;
   s = scratch_for_current_device(&scratch);
@@ -83,21 +77,23 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
 
   // Size check: the fixed part must fit; the rest of the array bounds the tile rows and
-  // instances (36 bytes per unit of capacity).
+  // instances (kBytesPerCapacity bytes per unit of capacity).
   Work w;
   w.n_views = n_views;
   w.n = n;
   w.tiles = tiles;
+  w.trows = trows;
+  w.max_tiles_x = max_tx;
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  const Layout L0 = make_layout(n_views, n, tiles, 0, w.G, false);
+  const Layout L0 = make_layout(n_views, n, tiles, trows, 0, w.G, false);
   if (L0.total + 8192 > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
-  int64_t cap = int64_t((kNoAllocScratchBytes - L0.total - 8192) / 37);
-  w.L = make_layout(n_views, n, tiles, cap, w.G, false);
+  int64_t cap = int64_t((kNoAllocScratchBytes - L0.total - 8192) / (kBytesPerCapacity + 1));
+  w.L = make_layout(n_views, n, tiles, trows, cap, w.G, false);
   while (w.L.total > kNoAllocScratchBytes && cap > 0) {
     cap -= 4096;
-    w.L = make_layout(n_views, n, tiles, cap, w.G, false);
+    w.L = make_layout(n_views, n, tiles, trows, cap, w.G, false);
   }
   if (cap <= 0 || w.L.total > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   w.cap = cap;

@@ -72,7 +72,7 @@ int tile_sort_bits(int64_t tiles) {
   return b;
 }
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bool backward) {
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, bool backward) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = up256(o + bytes); return r; };
@@ -81,6 +81,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bo
   L.cams = take(sizeof(DevCam) * size_t(n_views));
   L.counters = take(sizeof(Counters));
   L.evals = take(2 * sizeof(unsigned long long));
+  L.tscan = take(2 * sizeof(unsigned long long));
   L.depth = take(4 * VN);
   L.rect = take(8 * VN);
   L.ell = take(sizeof(Ell) * VN);
@@ -91,12 +92,15 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bo
   L.partial = take(4 * size_t(G));
   L.rtstart_len = uint32_t(C / kEmitTile + 2);
   L.rtstart = take(4 * size_t(L.rtstart_len));
+  // per unit of capacity: kBytesPerCapacity bytes
   L.seg = take(8 * C + 16);
   L.seg_len = take(4 * C + 16);
   L.seg_off = take(4 * C + 16);
-  L.itstart_len = uint32_t(C / kEmitTile + 2);
-  L.itstart = take(4 * size_t(L.itstart_len));
-  for (int i = 0; i < 2; ++i) { L.ik[i] = take(4 * C + 16); L.iv[i] = take(4 * C + 16); }
+  for (int i = 0; i < 2; ++i) { L.rk[i] = take(4 * C + 16); L.rv[i] = take(8 * C + 16); }
+  L.inst = take(4 * C + 16);
+  L.trange = take(8 * size_t(trows) + 16);
+  L.tcnt = take(4 * size_t(tiles) + 16);
+  L.toff = take(4 * size_t(tiles) + 16);
   L.hist = take(4 * 512 * size_t(G) + 4 * (512 * size_t(G) / 2048 + 1));
   L.ranges = take(8 * size_t(tiles));
   L.deg = take(4 * VN);
@@ -107,10 +111,29 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bo
   return L;
 }
 
+bool plan_views(const raygs_camera *cams, int n_views, const raygs_config &cfg, DevCam *dc, int64_t &tiles,
+                int64_t &trows, int64_t &pixels, int &max_tiles_x) {
+  tiles = 0; trows = 0; pixels = 0; max_tiles_x = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (!camera_valid(cams[v])) return false;
+    fill_devcam(cams[v], cfg, dc[v]);
+    if (dc[v].tiles_x > kMaxTilesX) return false;
+    dc[v].tile_base = int(tiles);
+    dc[v].trow_base = int(trows);
+    dc[v].pix_base = pixels;
+    tiles += int64_t(dc[v].tiles_x) * dc[v].tiles_y;
+    trows += dc[v].tiles_y;
+    pixels += int64_t(cams[v].width) * cams[v].height;
+    if (dc[v].tiles_x > max_tiles_x) max_tiles_x = dc[v].tiles_x;
+    if (tiles >= (int64_t(1) << 31)) return false;
+  }
+  return true;
+}
+
 cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(w.base + w.L.counters, 0, sizeof(Counters), st);
   if (e != cudaSuccess) return e;
-  PrepParams P;
+  PrepParams P{};
   P.means = scene.means;
   P.log_scales = scene.log_scales;
   P.quats = scene.quats;
@@ -148,7 +171,7 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   // 1. depth sort of the visible pairs: 4 passes of 8 bits over the float32 key
   int cur = 0;
   for (int pass = 0; pass < 4; ++pass) {
-    SortPass sp;
+    SortPass sp{};
     sp.keys_in = w.at<uint32_t>(pass == 0 ? w.L.depth : w.L.s1k[cur]);
     sp.vals_in = pass == 0 ? nullptr : w.at<uint32_t>(w.L.s1v[cur]);
     const int dst = pass == 0 ? 0 : 1 - cur;
@@ -170,7 +193,7 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   // 2a. pairs -> tile rows
   if ((e = launch_count_rows(pairs, w.at<uint2>(w.L.rect), w.at<uint32_t>(w.L.cnt), ctr, w.G, st)) != cudaSuccess)
     return e;
-  ScanJob J;
+  ScanJob J{};
   J.cnt = w.at<uint32_t>(w.L.cnt);
   J.off = w.at<uint32_t>(w.L.off);
   J.d_n = &ctr->n_visible;
@@ -183,7 +206,7 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   J.d_overflow = &ctr->overflow;
   if ((e = launch_scan(J, w.G, st)) != cudaSuccess) return e;
   // 2b. rows -> tile spans inside the support ellipse
-  RowsParams R;
+  RowsParams R{};
   R.pairs = pairs;
   R.rect = w.at<uint2>(w.L.rect);
   R.ell = w.at<Ell>(w.L.ell);
@@ -197,66 +220,87 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   R.tile_h = w.cfg.tile_h;
   R.seg = w.at<uint2>(w.L.seg);
   R.seg_len = w.at<uint32_t>(w.L.seg_len);
+  R.row_key = w.at<uint32_t>(w.L.rk[0]);
   if ((e = launch_rows(R, w.G, st)) != cudaSuccess) return e;
-  ScanJob J2;
+  ScanJob J2{};
   J2.cnt = R.seg_len;
   J2.off = w.at<uint32_t>(w.L.seg_off);
   J2.d_n = &ctr->n_rows_clamped;
   J2.partial = w.at<uint32_t>(w.L.partial);
-  J2.tile_start = w.at<uint32_t>(w.L.itstart);
-  J2.tstart_len = w.L.itstart_len;
+  J2.tile_start = nullptr;
+  J2.tstart_len = 0;
   J2.d_total = &ctr->n_instances;
   J2.d_total_clamped = &ctr->n_inst_clamped;
   J2.cap = cap;
   J2.d_overflow = &ctr->overflow;
   if ((e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
-  // 2c. rows -> instances (tile id, sorted pair position), in depth order
-  EmitParams E;
-  E.seg = R.seg;
-  E.seg_off = J2.off;
-  E.tile_start = J2.tile_start;
-  E.pairs = pairs;
-  E.cams = R.cams;
-  E.counters = ctr;
-  E.n = int(w.n);
-  E.keys = w.at<uint32_t>(w.L.ik[0]);
-  E.vals = w.at<uint32_t>(w.L.iv[0]);
-  if ((e = launch_emit(E, w.G, st)) != cudaSuccess) return e;
-  // 3. stable sort of instances by tile id (9-bit digits)
-  const int bits = tile_sort_bits(w.tiles);
-  const int passes = (bits + 8) / 9;
+  // 3. stable sort of the non-empty rows by global tile row (8-bit digits); the first
+  // pass drops the empty rows and gathers each row's payload
+  const int rbits = tile_sort_bits(w.trows);
+  const int rpasses = (rbits + 7) / 8;
   cur = 0;
-  for (int pass = 0; pass < passes; ++pass) {
-    SortPass sp;
-    sp.keys_in = w.at<uint32_t>(w.L.ik[cur]);
-    sp.vals_in = w.at<uint32_t>(w.L.iv[cur]);
-    sp.keys_out = w.at<uint32_t>(w.L.ik[1 - cur]);
-    sp.vals_out = w.at<uint32_t>(w.L.iv[1 - cur]);
-    sp.d_count = &ctr->n_inst_clamped;
+  for (int pass = 0; pass < rpasses; ++pass) {
+    SortPass sp{};
+    sp.keys_in = w.at<uint32_t>(w.L.rk[pass == 0 ? 0 : cur]);
+    sp.vals_in = nullptr;
+    const int dst = pass == 0 ? 1 : 1 - cur;
+    sp.keys_out = w.at<uint32_t>(w.L.rk[dst]);
+    sp.vals_out = nullptr;
+    sp.d_count = pass == 0 ? &ctr->n_rows_clamped : &ctr->n_rows_kept;
     sp.count_max = cap;
-    sp.shift = 9 * pass;
-    sp.bits = 9;
-    sp.filter = 0;
+    sp.shift = 8 * pass;
+    sp.bits = 8;
+    sp.filter = pass == 0 ? 1 : 0;
     sp.hist = hist;
     sp.G = w.G;
-    sp.d_total = nullptr;
+    sp.d_total = pass == 0 ? &ctr->n_rows_kept : nullptr;
+    sp.wide = 1;
+    sp.wvals_in = w.at<uint2>(w.L.rv[cur]);
+    sp.wvals_out = w.at<uint2>(w.L.rv[dst]);
+    sp.seg = R.seg;
+    sp.seg_len = R.seg_len;
     if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
-    cur = 1 - cur;
+    cur = dst;
   }
-  w.s2_final = cur;
-  // 4. tile ranges
-  uint2 *ranges = w.at<uint2>(w.L.ranges);
-  if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * size_t(w.tiles), st)) != cudaSuccess) return e;
-  return launch_ranges(w.at<uint32_t>(w.L.ik[cur]), ctr, ranges, w.G, st);
+  w.s2_rows = cur;
+  // 4. tile-row ranges of the sorted rows, instances per tile, tile offsets, lists
+  uint2 *trange = w.at<uint2>(w.L.trange);
+  if ((e = cudaMemsetAsync(trange, 0, sizeof(uint2) * size_t(w.trows), st)) != cudaSuccess) return e;
+  if ((e = launch_ranges(w.at<uint32_t>(w.L.rk[cur]), &ctr->n_rows_kept, trange, w.G, st)) != cudaSuccess) return e;
+  ExpandParams X{};
+  X.cams = R.cams;
+  X.n_views = w.n_views;
+  X.trow_ranges = trange;
+  X.rows = w.at<uint2>(w.L.rv[cur]);
+  X.tile_cnt = w.at<uint32_t>(w.L.tcnt);
+  X.tile_off = w.at<uint32_t>(w.L.toff);
+  X.ranges = w.at<uint2>(w.L.ranges);
+  X.inst = w.at<uint32_t>(w.L.inst);
+  X.cap = cap;
+  if ((e = launch_tile_counts(X, int(w.trows), w.max_tiles_x, st)) != cudaSuccess) return e;
+  ScanJob J3{};
+  J3.cnt = X.tile_cnt;
+  J3.off = w.at<uint32_t>(w.L.toff);
+  J3.d_n = nullptr;
+  J3.n_static = uint32_t(w.tiles);
+  J3.partial = w.at<uint32_t>(w.L.partial);
+  J3.tile_start = nullptr;
+  J3.tstart_len = 0;
+  J3.d_total = w.at<unsigned long long>(w.L.tscan);
+  J3.d_total_clamped = reinterpret_cast<uint32_t *>(w.at<unsigned long long>(w.L.tscan) + 1);
+  J3.cap = cap;
+  J3.d_overflow = &ctr->overflow;
+  if ((e = launch_scan(J3, w.G, st)) != cudaSuccess) return e;
+  return launch_expand(X, int(w.trows), w.max_tiles_x, st);
 }
 
 cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_contrib, bool count,
                        cudaStream_t st) {
-  RenderParams P;
+  RenderParams P{};
   P.cams = w.at<DevCam>(w.L.cams);
   P.n_views = w.n_views;
   P.ranges = w.at<uint2>(w.L.ranges);
-  P.inst_vals = w.at<uint32_t>(w.L.iv[w.s2_final]);
+  P.inst_vals = w.at<uint32_t>(w.L.inst);
   P.pairs = w.at<uint32_t>(w.L.s1v[w.s1_final]);
   P.rec = w.at<Rec>(w.L.rec);
   P.t_stop = w.cfg.t_stop;
@@ -274,11 +318,11 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
 
 cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T_final, const int32_t *n_contrib,
                          const float *dL_drgb, const float *dL_dT, const raygs_grads &grads, cudaStream_t st) {
-  BackParams B;
+  BackParams B{};
   B.cams = w.at<DevCam>(w.L.cams);
   B.n_views = w.n_views;
   B.ranges = w.at<uint2>(w.L.ranges);
-  B.inst_vals = w.at<uint32_t>(w.L.iv[w.s2_final]);
+  B.inst_vals = w.at<uint32_t>(w.L.inst);
   B.pairs = w.at<uint32_t>(w.L.s1v[w.s1_final]);
   B.rec = w.at<Rec>(w.L.rec);
   B.rect = w.at<uint2>(w.L.rect);
@@ -294,7 +338,7 @@ cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T
   B.partials = w.at<float>(w.L.partials);
   cudaError_t e = launch_render_backward(B, w.cfg.tile_w, w.cfg.tile_h, w.tiles, st);
   if (e != cudaSuccess) return e;
-  PairGradParams Q;
+  PairGradParams Q{};
   Q.pairs = B.pairs;
   Q.row_off = B.row_off;
   Q.seg_off = B.seg_off;
@@ -302,7 +346,7 @@ cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T
   Q.partials = B.partials;
   Q.pg = w.at<float>(w.L.pg);
   if ((e = launch_pair_grads(Q, w.G, st)) != cudaSuccess) return e;
-  ParamGradParams R;
+  ParamGradParams R{};
   R.means = scene.means;
   R.log_scales = scene.log_scales;
   R.quats = scene.quats;

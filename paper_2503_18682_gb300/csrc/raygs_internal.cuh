@@ -26,7 +26,7 @@ struct DevCam {
   float xmin, xmax, ymin, ymax;  // slopes of the outermost pixel-centre rays
   int tiles_x, tiles_y;
   int tile_base;               // first global tile id of the view
-  int pad0;
+  int trow_base;               // first global tile row of the view
   long long pix_base;          // first output pixel of the view
 };
 
@@ -50,7 +50,7 @@ struct Counters {
   unsigned long long n_instances;
   unsigned long long n_nonfinite;
   uint32_t n_fp64;          // (primitive, view) pairs recomputed in FP64
-  uint32_t pad;
+  uint32_t n_rows_kept;     // support rows with at least one tile
 };
 
 // Screen-space support ellipse of a (primitive, view): pixel centres p with
@@ -176,6 +176,13 @@ struct SortPass {
   uint32_t *hist;           // [512][G]
   int G;
   uint32_t *d_total;        // receives the number of items kept (nullable)
+  // wide mode (tile-row sort of the support rows): 8-byte values (sorted pair position,
+  // first tile column | run length << 16); the filter pass reads them from seg / seg_len
+  int wide;
+  const uint2 *wvals_in;
+  uint2 *wvals_out;
+  const uint2 *seg;
+  const uint32_t *seg_len;
 };
 
 // Exclusive scan of per-unit output counts, with the unit that holds the first output of
@@ -183,7 +190,8 @@ struct SortPass {
 struct ScanJob {
   const uint32_t *cnt;
   uint32_t *off;
-  const uint32_t *d_n;      // number of units (device)
+  const uint32_t *d_n;      // number of units (device; nullable: n_static is used)
+  uint32_t n_static;
   uint32_t *partial;        // [G]
   uint32_t *tile_start;
   uint32_t tstart_len;
@@ -206,18 +214,21 @@ struct RowsParams {
   int tile_w, tile_h;
   uint2 *seg;               // per row: (sorted pair position, ty | txa << 16)
   uint32_t *seg_len;        // per row: tiles of the row inside the support
+  uint32_t *row_key;        // per row: global tile row, or kCulled when the run is empty
 };
 
-struct EmitParams {
-  const uint2 *seg;
-  const uint32_t *seg_off;
-  const uint32_t *tile_start;
-  const uint32_t *pairs;
+// Per-tile-row passes over the support rows sorted by tile row (stable, so each tile row
+// lists its rows in depth order): per-tile instance counts, then the instance lists.
+struct ExpandParams {
   const DevCam *cams;
-  const Counters *counters;
-  int n;
-  uint32_t *keys;           // [capacity] global tile id
-  uint32_t *vals;           // [capacity] sorted pair position
+  int n_views;
+  const uint2 *trow_ranges;  // [tile rows] range of the tile row in the sorted rows
+  const uint2 *rows;         // sorted rows: (sorted pair position, txa | len << 16)
+  uint32_t *tile_cnt;        // [tiles] instances per tile
+  const uint32_t *tile_off;  // [tiles] exclusive scan of tile_cnt
+  uint2 *ranges;             // [tiles] instance range of every tile (clamped to cap)
+  uint32_t *inst;            // [cap] sorted pair position of every instance
+  uint32_t cap;
 };
 
 struct RenderParams {
@@ -235,6 +246,7 @@ struct RenderParams {
 };
 
 constexpr int kEmitTile = 2048;
+constexpr int kMaxTilesX = 4096;  // tiles in one tile row (32768-pixel views at 8-pixel tiles)
 constexpr int kGradW = 13;  // per-instance / per-pair gradient partials (see backward.cu)
 
 struct BackParams {
@@ -290,8 +302,9 @@ cudaError_t launch_count_rows(const uint32_t *pairs, const uint2 *rect, uint32_t
                               cudaStream_t st);
 cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
-cudaError_t launch_emit(const EmitParams &E, int G, cudaStream_t st);
-cudaError_t launch_ranges(const uint32_t *keys, const Counters *c, uint2 *ranges, int G, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
+cudaError_t launch_tile_counts(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
+cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
                           cudaStream_t st);
 cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
@@ -301,28 +314,36 @@ cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t cams, counters, evals, depth, rect, ell, rec, s1k[2], s1v[2], cnt, off, partial, rtstart,
-      seg, seg_len, seg_off, itstart, ik[2], iv[2], hist, ranges, deg, degc, partials, pg, total;
-  uint32_t rtstart_len, itstart_len;
+  size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], cnt, off, partial, rtstart,
+      seg, seg_len, seg_off, rk[2], rv[2], trange, tcnt, toff, inst, hist, ranges, deg, degc, partials, pg, total;
+  uint32_t rtstart_len;
 };
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t cap, int G, bool backward);
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, bool backward);
+
+// Workspace bytes per unit of instance capacity (tile rows and instances share it).
+constexpr size_t kBytesPerCapacity = 8 + 4 + 4 + 2 * 4 + 2 * 8 + 4;
 
 // A bound workspace and the sizes it was laid out for.
 struct Work {
   char *base = nullptr;
   Layout L{};
   int n_views = 0;
-  int64_t n = 0, tiles = 0, cap = 0;
+  int64_t n = 0, tiles = 0, trows = 0, cap = 0;
+  int max_tiles_x = 0;
   int G = 0, num_sms = 0;
   raygs_config cfg{};
-  int s1_final = 0, s2_final = 0;  // which ping-pong buffers hold the sorted results
+  int s1_final = 0, s2_rows = 0;  // which ping-pong buffers hold the sorted results
   template <typename T>
   T *at(size_t off) const { return reinterpret_cast<T *>(base + off); }
 };
 
 // Host-side helpers shared by the entry points.
 void fill_devcam(const raygs_camera &c, const raygs_config &cfg, DevCam &d);
+// Per-view constants and the global tile, tile-row and pixel numbering of a batch of views;
+// false when a view is invalid or the batch is too large to number in 31 bits.
+bool plan_views(const raygs_camera *cams, int n_views, const raygs_config &cfg, DevCam *dc, int64_t &tiles,
+                int64_t &trows, int64_t &pixels, int &max_tiles_x);
 bool config_valid(const raygs_config &cfg);
 bool camera_valid(const raygs_camera &c);
 raygs_status scene_valid(const raygs_scene *s, int64_t n);

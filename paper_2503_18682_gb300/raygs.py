@@ -46,7 +46,8 @@ class Scene(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("n_instances", C.c_int64), ("capacity", C.c_int64),
-                ("n_nonfinite", C.c_int64), ("overflow", C.c_int32)]
+                ("n_nonfinite", C.c_int64), ("overflow", C.c_int32), ("pad", C.c_int32),
+                ("n_rows", C.c_int64), ("n_rows_kept", C.c_int64)]
 
 
 class Grads(C.Structure):
@@ -252,7 +253,7 @@ def raygs_read_counters(plan, stream=None) -> dict:
     c = Counters()
     _check(lib().raygs_read_counters(plan, C.byref(c), stream_ptr(stream)), "raygs_read_counters")
     return dict(n_visible=c.n_visible, n_instances=c.n_instances, capacity=c.capacity,
-                n_nonfinite=c.n_nonfinite, overflow=c.overflow)
+                n_nonfinite=c.n_nonfinite, overflow=c.overflow, n_rows=c.n_rows, n_rows_kept=c.n_rows_kept)
 
 
 def raygs_graph_capture(plan, scene: Scene, rgb, T_final=None, n_contrib=None, stream=None):

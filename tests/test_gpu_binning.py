@@ -38,6 +38,18 @@ def fetch(ptr, count, dtype):
     return t.cpu().numpy().view(dtype).copy()
 
 
+def instance_lists(r, ni):
+    """(tile id, sorted pair position) of every instance.  The tile ranges must partition
+    the instance array in tile order."""
+    ranges = fetch(r.debug_buffer(6), 2 * r.num_tiles, np.uint32).reshape(-1, 2).astype(np.int64)
+    assert ranges[0, 0] == 0 and ranges[-1, 1] == ni
+    np.testing.assert_array_equal(ranges[1:, 0], ranges[:-1, 1])
+    assert np.all(ranges[:, 1] >= ranges[:, 0])
+    g_tiles = np.repeat(np.arange(r.num_tiles, dtype=np.int64), ranges[:, 1] - ranges[:, 0])
+    g_pos = fetch(r.debug_buffer(5), ni, np.uint32).astype(np.int64)
+    return g_tiles, g_pos
+
+
 def tile_base_of(r, v):
     tw, th = r.cfg.tile_w, r.cfg.tile_h
     return sum((-(-c["width"] // tw)) * (-(-c["height"] // th)) for c in r.cams[:v])
@@ -72,18 +84,9 @@ def test_sort_and_tile_lists(oracle_lib, tile):
     g_order = fetch(r.debug_buffer(3), len(order), np.uint32)
     np.testing.assert_array_equal(g_order, order)
     ni = ctr["n_instances"]
-    g_tiles = fetch(r.debug_buffer(4), ni, np.uint32).astype(np.int64)
-    g_pos = fetch(r.debug_buffer(5), ni, np.uint32).astype(np.int64)
-    assert np.all(np.diff(g_tiles) >= 0)
+    g_tiles, g_pos = instance_lists(r, ni)
     same = np.diff(g_tiles) == 0
     assert np.all(np.diff(g_pos)[same] > 0)             # depth order inside a tile
-    ranges = fetch(r.debug_buffer(6), 2 * r.num_tiles, np.uint32).reshape(-1, 2)
-    starts = np.searchsorted(g_tiles, np.arange(r.num_tiles), side="left")
-    ends = np.searchsorted(g_tiles, np.arange(r.num_tiles), side="right")
-    nonempty = ends > starts
-    np.testing.assert_array_equal(ranges[nonempty, 0], starts[nonempty])
-    np.testing.assert_array_equal(ranges[nonempty, 1], ends[nonempty])
-    assert np.all(ranges[~nonempty, 0] == ranges[~nonempty, 1])
     # instances inside the rectangles; dropped rectangle tiles miss the support
     kept = {}
     for t, p in zip(g_tiles, g_pos):
@@ -128,9 +131,7 @@ def assert_dropped_tiles_miss_support(oracle_lib, scene, cams, r, n, tile, pairs
     rects = fetch(r.debug_buffer(1), 2 * n * len(cams), np.uint32).reshape(-1, 2)
     ctr = r.last_counters
     order = fetch(r.debug_buffer(3), ctr["n_visible"], np.uint32)
-    ni = ctr["n_instances"]
-    g_tiles = fetch(r.debug_buffer(4), ni, np.uint32).astype(np.int64)
-    g_pos = fetch(r.debug_buffer(5), ni, np.uint32).astype(np.int64)
+    g_tiles, g_pos = instance_lists(r, ctr["n_instances"])
     kept = {}
     for t, p in zip(g_tiles, g_pos):
         kept.setdefault(int(p), set()).add(int(t))
