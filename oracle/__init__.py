@@ -9,6 +9,6 @@ same image used only to obtain reference gradients by autograd.  ``build()`` com
 C file with gcc (-O2 -fopenmp -ffp-contract=off).
 """
 from .raygs_oracle import (  # noqa: F401
-    build, lib, cam_array, cfg_array, prepare, render, quad, rot_align, D_ray, sh_basis,
+    build, lib, cam_array, cfg_array, prepare, render, quad, rot_align, D_ray, support_mask, sh_basis,
     quat_to_rot, depth_key, DEFAULT_CFG, OG,
 )

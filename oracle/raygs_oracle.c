@@ -178,6 +178,20 @@ double oracle_D_ray(const double mu[3], const double Si[9], const double x[3], d
   return D;
 }
 
+/* Support of one primitive over a pixel rectangle [x0, x0+w) x [y0, y0+h): out[j*w+i] = 1
+ * when the ray through the centre of pixel (x0+i, y0+j) has tau > 0 and D <= kappa
+ * (Eq. Q_ray and the cut-off of Sec. 3), else 0.  cam = (fx, fy, cx, cy). */
+void oracle_support_mask(const double mu[3], const double Si[9], double kappa, const double cam[4], int x0, int y0,
+                         int w, int h, unsigned char *out) {
+  for (int j = 0; j < h; ++j)
+    for (int i = 0; i < w; ++i) {
+      const double x[3] = {((x0 + i) + 0.5 - cam[2]) / cam[0], ((y0 + j) + 0.5 - cam[3]) / cam[1], 1.0};
+      double tau;
+      const double D = oracle_D_ray(mu, Si, x, &tau);
+      out[j * w + i] = (tau > 0.0 && D <= kappa) ? 1 : 0;
+    }
+}
+
 /* App. A.1: R_{x,y} = 2 (x+y)(x+y)^T / |x+y|^2 - I (aligns y to x). */
 static void rot_xy(const double x[3], const double y[3], double R[9]) {
   double a[3] = {x[0] + y[0], x[1] + y[1], x[2] + y[2]};

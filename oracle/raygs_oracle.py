@@ -51,6 +51,8 @@ def lib():
         L.oracle_rot_align.restype = None
         L.oracle_D_ray.argtypes = [P, P, P, P]
         L.oracle_D_ray.restype = C.c_double
+        L.oracle_support_mask.argtypes = [P, P, C.c_double, P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+        L.oracle_support_mask.restype = None
         L.oracle_sh_basis.argtypes = [C.c_int, P, P]
         L.oracle_sh_basis.restype = None
         L.oracle_quat_to_rot.argtypes = [P, P]
@@ -163,6 +165,17 @@ def D_ray(mu, Sigma_inv, x):
     tau = np.zeros(1, dtype=np.float64)
     D = lib().oracle_D_ray(_p(mu), _p(Si), _p(x), _p(tau))
     return float(D), float(tau[0])
+
+
+def support_mask(mu, Sigma_inv, kappa, cam, x0, y0, w, h) -> np.ndarray:
+    """Pixels of the rectangle [x0, x0+w) x [y0, y0+h) whose centre ray has tau > 0 and
+    D <= kappa (Eq. Q_ray with the cut-off): bool array [h, w]."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    Si = np.ascontiguousarray(Sigma_inv, dtype=np.float64).reshape(9)
+    c = np.array([float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])], dtype=np.float64)
+    out = np.zeros(h * w, dtype=np.uint8)
+    lib().oracle_support_mask(_p(mu), _p(Si), float(kappa), _p(c), int(x0), int(y0), int(w), int(h), _p(out))
+    return out.reshape(h, w).astype(bool)
 
 
 def sh_basis(degree: int, d) -> np.ndarray:

@@ -445,15 +445,17 @@ __device__ __forceinline__ bool ellipse_band(const Ell &e, float ya, float yb, f
 // Supports that are not a bounded ellipse (the primitive's cone of rays reaches the
 // camera plane, or the ellipse is too ill-conditioned in float32) are still convex: the
 // image of one nappe of an elliptic cone cut by the plane z = 1.  Within a band of pixel
-// rows their pixels therefore occupy one contiguous run of tiles, found by testing tile
-// rectangles from both ends of the row.
+// rows their pixels therefore occupy one contiguous run of tiles, whose ends are found by
+// bisection with a vertical-line test.
 
 // Does the segment delta(t) = P + t E, t in [0, 1] (pixel offsets from the projected
 // centre) meet the support kp |G delta|^2 <= y2^2, y2 = 1 + h.delta > 0?  Along the
 // segment y01 = a + t b and y2 = al + t be, so f = kp |y01|^2 - y2^2 is a quadratic in t;
 // its minimum over the part where y2 > 0 is compared with a margin of 1e-4 of the
 // magnitude of its terms, far above float32 rounding: the answer errs only towards yes.
-__device__ __forceinline__ bool segment_meets_support(const Rec &r, float Px, float Py, float Ex, float Ey) {
+// t_at receives the parameter of that minimum.
+__device__ __forceinline__ bool segment_meets_support(const Rec &r, float Px, float Py, float Ex, float Ey,
+                                                      float *t_at = nullptr) {
   const float kp = r.c.z;
   const float a0 = fmaf(r.b.x, Px, r.b.y * Py), a1 = fmaf(r.b.z, Px, r.b.w * Py);
   const float b0 = fmaf(r.b.x, Ex, r.b.y * Ey), b1 = fmaf(r.b.z, Ex, r.b.w * Ey);
@@ -469,34 +471,86 @@ __device__ __forceinline__ bool segment_meets_support(const Rec &r, float Px, fl
   const float Bh = fmaf(kp, qab, -al * be);
   const float Cc = fmaf(kp, qa, -al * al);
   const float margin = 1e-4f * (2.f * fmaf(kp, qa, al * al) + 2.f * fmaf(kp, qb, be * be)) + 1e-6f;
-  float m = fminf(fmaf(fmaf(A, t0, 2.f * Bh), t0, Cc), fmaf(fmaf(A, t1, 2.f * Bh), t1, Cc));
+  const float f0 = fmaf(fmaf(A, t0, 2.f * Bh), t0, Cc), f1 = fmaf(fmaf(A, t1, 2.f * Bh), t1, Cc);
+  float m = f0, tm = t0;
+  if (f1 < m) { m = f1; tm = t1; }
   if (A > 0.f) {
     const float tv = -Bh / A;
-    if (tv > t0 && tv < t1) m = fminf(m, fmaf(Bh, tv, Cc));
+    if (tv > t0 && tv < t1) {
+      const float fv = fmaf(Bh, tv, Cc);
+      if (fv < m) { m = fv; tm = tv; }
+    }
   }
+  if (t_at) *t_at = tm;
   return m <= margin;
 }
 
-// First (from_left) or last tile column in [tx0, tx1] whose pixel centres in rows
-// [ya, yb] can meet the support; -1 if none.
-__device__ int support_tile_end(const Rec &r, const DevCam &cam, int tile_w, float ya, float yb, int tx0, int tx1,
-                                bool from_left) {
+// Can the pixel centres of the rectangle [dxa, dxb] x [dya, dyb] (offsets from the projected
+// centre) meet the support?  For a convex support: the rectangle holds the projected centre,
+// or one of its edges meets the support.
+__device__ __forceinline__ bool tile_meets_support(const Rec &r, float dxa, float dxb, float dya, float dyb) {
+  return (dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) ||
+         segment_meets_support(r, dxa, dya, 0.f, dyb - dya) || segment_meets_support(r, dxb, dya, 0.f, dyb - dya) ||
+         segment_meets_support(r, dxa, dya, dxb - dxa, 0.f) || segment_meets_support(r, dxa, dyb, dxb - dxa, 0.f);
+}
+
+// First and last tile column in [tx0, tx1] whose pixel centres in rows [ya, yb] can meet
+// the support; false if none.  A point of the support inside the band is found on the
+// band's boundary or is the projected centre itself (a convex set that meets a rectangle
+// but not its boundary lies inside it).  Left of that point, tile t meets the support
+// exactly when the vertical line through its last pixel-centre column does (the support's
+// columns within the band form an interval), and symmetrically on the right.
+__device__ bool support_tile_span(const Rec &r, const DevCam &cam, int tile_w, float ya, float yb, int tx0, int tx1,
+                                  int &first, int &last) {
   const float ux = r.a.x, uy = r.a.y, lx = r.a.z, ly = r.a.w;
   const float dya = (ya - uy) - ly, dyb = (yb - uy) - ly;
-  const int n = tx1 - tx0 + 1;
-  for (int i = 0; i < n; ++i) {
-    const int tx = from_left ? tx0 + i : tx1 - i;
-    const float xa = float(tx * tile_w) + 0.5f;
-    const float xb = float(min((tx + 1) * tile_w, cam.W)) - 0.5f;
-    const float dxa = (xa - ux) - lx, dxb = (xb - ux) - lx;
-    if ((dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) ||      // the centre itself
-        segment_meets_support(r, dxa, dya, 0.f, dyb - dya) ||
-        segment_meets_support(r, dxb, dya, 0.f, dyb - dya) ||
-        segment_meets_support(r, dxa, dya, dxb - dxa, 0.f) ||
-        segment_meets_support(r, dxa, dyb, dxb - dxa, 0.f))
-      return tx;
+  auto col_dx = [&](int px_centre_times2) {  // pixel-centre column (2x, exact) as an offset
+    return (0.5f * float(px_centre_times2) - ux) - lx;
+  };
+  auto left_col = [&](int tx) { return col_dx(2 * tx * tile_w + 1); };
+  auto right_col = [&](int tx) { return col_dx(2 * min((tx + 1) * tile_w, cam.W) - 1); };
+  auto vert = [&](float dx) { return segment_meets_support(r, dx, dya, 0.f, dyb - dya); };
+  const float dxL = left_col(tx0), dxR = right_col(tx1);
+  // a tile that holds a point of the support (any tile at least as wide as that point's
+  // pixel column is a conservative choice)
+  int tstar = -1;
+  float t;
+  if (vert(dxL)) {
+    tstar = tx0;
+  } else if (vert(dxR)) {
+    tstar = tx1;
+  } else {
+    float cx = 0.f;
+    bool inside = dya <= 0.f && dyb >= 0.f && dxL <= 0.f && dxR >= 0.f;
+    if (!inside && segment_meets_support(r, dxL, dya, dxR - dxL, 0.f, &t)) { inside = true; cx = fmaf(t, dxR - dxL, dxL); }
+    if (!inside && segment_meets_support(r, dxL, dyb, dxR - dxL, 0.f, &t)) { inside = true; cx = fmaf(t, dxR - dxL, dxL); }
+    if (!inside) return false;
+    // the minimum along a long horizontal segment carries a wide margin: confirm the point
+    // with the (short) vertical test, else scan the row tile by tile
+    if (!vert(cx)) {
+      for (first = tx0; first <= tx1; ++first)
+        if (tile_meets_support(r, left_col(first), right_col(first), dya, dyb)) break;
+      if (first > tx1) return false;
+      for (last = tx1; last > first; --last)
+        if (tile_meets_support(r, left_col(last), right_col(last), dya, dyb)) break;
+      return true;
+    }
+    const float px = (cx + lx) + ux;  // pixel x of the point
+    tstar = min(max(int(floorf(px / float(tile_w))), tx0), tx1);
   }
-  return -1;
+  int lo = tx0, hi = tstar;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (vert(right_col(mid))) hi = mid; else lo = mid + 1;
+  }
+  first = lo;
+  lo = tstar; hi = tx1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (vert(left_col(mid))) lo = mid; else hi = mid - 1;
+  }
+  last = lo;
+  return true;
 }
 
 __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
@@ -535,12 +589,12 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
       const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
       if (el.rho < 0.f) {
         const Rec rc = R.rec[pair];
-        const int a0 = support_tile_end(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), true);
-        if (a0 < 0) {
+        int a0, b0;
+        if (!support_tile_span(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), a0, b0)) {
           empty = true;
         } else {
           xa_t = uint32_t(a0);
-          xb_t = uint32_t(support_tile_end(rc, cam, R.tile_w, ya, yb, a0, int(tx1), false));
+          xb_t = uint32_t(b0);
         }
       } else {
         float xa, xb;
@@ -667,9 +721,10 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
   __syncthreads();
   const DevCam &cam = E.cams[s_v];
   const int TX = cam.tiles_x;
+  const int TP = TX | 1;                     // odd row stride: no bank conflicts down a column
   uint32_t *s_cur = s_mem;                   // [TX] next free slot of each tile
-  uint32_t *s_pre = s_cur + TX;              // [VW][TX] first slot of each group
-  uint32_t *s_mask = s_pre + VW * TX;        // [2][VW][TX]
+  uint32_t *s_pre = s_cur + TX;              // [VW][TP] first slot of each group
+  uint32_t *s_mask = s_pre + VW * TP;        // [2][VW][TP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
@@ -678,7 +733,7 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
     s_cur[x] = o;
     E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + c, E.cap));
   }
-  for (int j = threadIdx.x; j < 2 * VW * TX; j += NT) s_mask[j] = 0u;
+  for (int j = threadIdx.x; j < 2 * VW * TP; j += NT) s_mask[j] = 0u;
   const uint2 rr = E.trow_ranges[grow];
   constexpr uint32_t STEP = uint32_t(NT) * KR;
   uint2 nxt[KR];
@@ -696,25 +751,32 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
 #pragma unroll
     for (int k = 0; k < KR; ++k) cur[k] = nxt[k];
     if (base + STEP < rr.y) load_rows(base + STEP);
-    uint32_t *mask = s_mask + buf * VW * TX;
+    uint32_t *mask = s_mask + buf * VW * TP;
     __syncthreads();  // masks of this buffer cleared; the previous step's reads are done
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
       const int g = k * (NT / 32) + warp;
       const uint32_t xa = cur[k].y & 0xFFFFu, len = cur[k].y >> 16;
-      for (uint32_t t = 0; t < len; ++t) atomicOr(&mask[g * TX + int(xa + t)], 1u << lane);
+      for (uint32_t t = 0; t < len; ++t) atomicOr(&mask[g * TP + int(xa + t)], 1u << lane);
     }
     __syncthreads();
-    uint32_t *other = s_mask + (1 - buf) * VW * TX;
-    for (int x = threadIdx.x; x < TX; x += NT) {
-      uint32_t run = s_cur[x];
-#pragma unroll 4
-      for (int g = 0; g < VW; ++g) {
-        s_pre[g * TX + x] = run;
-        run += __popc(mask[g * TX + x]);
-        other[g * TX + x] = 0u;
+    // per tile, a warp scans the group counts (lane g = group g)
+    uint32_t *other = s_mask + (1 - buf) * VW * TP;
+    for (int x = warp; x < TX; x += NT / 32) {
+      const uint32_t c = lane < VW ? __popc(mask[lane * TP + x]) : 0u;
+      uint32_t inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
       }
-      s_cur[x] = run;
+      const uint32_t run = s_cur[x];
+      if (lane < VW) {
+        s_pre[lane * TP + x] = run + inc - c;
+        other[lane * TP + x] = 0u;
+      }
+      __syncwarp();
+      if (lane == 31) s_cur[x] = run + inc;
     }
     __syncthreads();
 #pragma unroll
@@ -723,7 +785,7 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
       const uint32_t xa = cur[k].y & 0xFFFFu, len = cur[k].y >> 16;
       for (uint32_t t = 0; t < len; ++t) {
         const int x = int(xa + t);
-        const uint32_t dst = s_pre[g * TX + x] + __popc(mask[g * TX + x] & lt);
+        const uint32_t dst = s_pre[g * TP + x] + __popc(mask[g * TP + x] & lt);
         if (dst < E.cap) E.inst[dst] = cur[k].x;
       }
     }
@@ -733,7 +795,7 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
 
 template <int NT, int KR>
 size_t expand_smem(int max_tiles_x) {
-  return sizeof(uint32_t) * size_t(max_tiles_x) * size_t(1 + 3 * (NT / 32) * KR);
+  return sizeof(uint32_t) * size_t(max_tiles_x + 1) * size_t(1 + 3 * (NT / 32) * KR);
 }
 
 cudaError_t launch_tile_counts(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {

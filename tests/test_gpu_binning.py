@@ -88,32 +88,9 @@ def test_sort_and_tile_lists(oracle_lib, tile):
     same = np.diff(g_tiles) == 0
     assert np.all(np.diff(g_pos)[same] > 0)             # depth order inside a tile
     # instances inside the rectangles; dropped rectangle tiles miss the support
-    kept = {}
-    for t, p in zip(g_tiles, g_pos):
-        kept.setdefault(int(p), set()).add(int(t))
-    dropped_checked = 0
+    dropped, _, _ = assert_dropped_tiles_miss_support(oracle_lib, scene, cams, r, n, tile, {int(p) for p in order})
+    assert dropped > 0
     infos = [oracle_lib.prepare(scene, cam) for cam in cams]
-    for p, pair in enumerate(order):
-        v, g = divmod(int(pair), n)
-        x0, y0, x1, y1 = rect_of(rects, pair)
-        base = tile_base_of(r, v)
-        tx_n = -(-cams[v]["width"] // tw)
-        rect_tiles = {base + ty * tx_n + tx for ty in range(y0, y1 + 1) for tx in range(x0, x1 + 1)}
-        mine = kept.get(p, set())
-        assert mine <= rect_tiles, (p, pair)
-        info = infos[v][g]
-        Si = info[14:23].reshape(3, 3) @ np.diag(info[11:14] ** -2.0) @ info[14:23].reshape(3, 3).T
-        cam = cams[v]
-        for t in rect_tiles - mine:
-            ty, tx = divmod(t - base, tx_n)
-            for py in range(ty * th, min(ty * th + th, cam["height"])):
-                for px in range(tx * tw, min(tx * tw + tw, cam["width"])):
-                    x = [(px + 0.5 - float(cam["cx"])) / float(cam["fx"]),
-                         (py + 0.5 - float(cam["cy"])) / float(cam["fy"]), 1.0]
-                    D, tau = oracle_lib.D_ray(info[2:5], Si, x)
-                    assert not (tau > 0 and D <= info[6]), (pair, t, px, py)
-            dropped_checked += 1
-    assert dropped_checked > 0
     # depth keys equal the oracle's (same float32 chain), for every primitive the GPU kept
     for v, cam in enumerate(cams):
         info = infos[v]
@@ -154,12 +131,10 @@ def assert_dropped_tiles_miss_support(oracle_lib, scene, cams, r, n, tile, pairs
         cam = cams[v]
         for t in rect_tiles - mine:
             ty, tx = divmod(t - base, tx_n)
-            for py in range(ty * th, min(ty * th + th, cam["height"])):
-                for px in range(tx * tw, min(tx * tw + tw, cam["width"])):
-                    x = [(px + 0.5 - float(cam["cx"])) / float(cam["fx"]),
-                         (py + 0.5 - float(cam["cy"])) / float(cam["fy"]), 1.0]
-                    D, tau = oracle_lib.D_ray(info[2:5], Si, x)
-                    assert not (tau > 0 and D <= info[6]), (pair, t, px, py)
+            w = min(tw, cam["width"] - tx * tw)
+            h = min(th, cam["height"] - ty * th)
+            m = oracle_lib.support_mask(info[2:5], Si, info[6], cam, tx * tw, ty * th, w, h)
+            assert not m.any(), (pair, t)
             dropped += 1
     return dropped, n_rect, n_kept
 
@@ -179,7 +154,8 @@ def test_unbounded_supports_keep_every_covered_tile(oracle_lib, tile):
         rng.uniform([-1, -1, 0.3], [1, 1, 2.0], (n - n // 2, 3))]).astype(np.float32)
     sc["log_scales"] = rng.uniform(np.log(0.03), np.log(0.5), (n, 3)).astype(np.float32)
     R1, t1 = scenes.look_at([0.2, -0.1, -0.2], [0.0, 0.0, 1.0])
-    cams = [scenes.make_camera(96, 80, 70.0, 70.0), scenes.make_camera(120, 64, 60.0, 60.0, R=R1, t=t1)]
+    cams = [scenes.make_camera(96, 80, 70.0, 70.0), scenes.make_camera(120, 64, 60.0, 60.0, R=R1, t=t1),
+            scenes.make_camera(1200, 48, 300.0, 300.0)]    # long tile rows
     r, _, rgb, T, nc = gpu_render(sc, cams, tile_w=tile[0], tile_h=tile[1])
     ell = fetch(r.debug_buffer(7), 8 * n * len(cams), np.float32).reshape(-1, 8)
     order = fetch(r.debug_buffer(3), r.last_counters["n_visible"], np.uint32)

@@ -74,6 +74,25 @@ def test_closed_form_isotropic(oracle_lib):
         assert tau * np.linalg.norm(x) == pytest.approx(np.dot(mu, xh), rel=1e-10)
 
 
+def test_support_mask_isotropic_closed_form(oracle_lib):
+    """Support mask over a pixel rectangle for Sigma = s^2 I: a pixel is in the support
+    exactly when its ray passes within s sqrt(kappa) of the mean, in front of the camera
+    (closest-approach distance, D = |mu x x^|^2 / s^2).  Includes a mean behind the camera
+    plane, whose support must be empty."""
+    cam = dict(fx=40.0, fy=50.0, cx=20.0, cy=12.0)
+    for mu, s, kappa in (([0.1, -0.05, 1.0], 0.08, 9.0), ([-0.3, 0.2, 0.4], 0.05, 4.0),
+                         ([0.0, 0.0, -1.0], 0.3, 9.0)):
+        mu = np.array(mu)
+        m = oracle_lib.support_mask(mu, np.eye(3) / s ** 2, kappa, cam, -3, -2, 47, 29)
+        jj, ii = np.mgrid[-2:27, -3:44]
+        X = np.stack([(ii + 0.5 - 20.0) / 40.0, (jj + 0.5 - 12.0) / 50.0, np.ones(ii.shape)], -1)
+        Xh = X / np.linalg.norm(X, axis=-1, keepdims=True)
+        dist2 = np.sum(np.cross(mu, Xh) ** 2, axis=-1)
+        expect = (dist2 <= kappa * s ** 2) & (Xh @ mu > 0)
+        assert np.array_equal(m, expect)
+        assert m.any() == (mu[2] > 0)
+
+
 def test_ray_march_bruteforce(oracle_lib):
     """Prop. A.1: tau(x) x is the density maximum along the ray.  Brute force: a dense march
     over t in (0, t_max] with three refinement levels finds the same minimum of the
