@@ -123,7 +123,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -133,7 +134,8 @@ def sum_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
@@ -324,10 +326,10 @@ def run_ours(args, world, rank, local):
     flops = FLOP_EVAL * evals + FLOP_COMP * comps
     peak_tf = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     ach_tf = flops / (stages["render_ms"] * 1e-3) / 1e12
-    # HBM view of the vertex stage: attributes read once, per visible pair 64+8+4 B written,
-    # plus the 4 B key of every (primitive, view)
+    # HBM view of the vertex stage: attributes read once; per visible pair the 64-B record,
+    # 8-B tile rectangle and 32-B support ellipse written; the 4-B key of every pair
     attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
-    prep_bytes = attr_bytes + 4 * n * len(cams) + 76 * ctr["n_visible"]
+    prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
     # kernels per pass: preprocess (2), depth sort (4 passes x 5), rows count + scan (4),
     # row spans (1), span scan (3), tile-row sort (passes x 5), tile-row ranges (1), tile
     # counts (1), tile scan (3), instance lists (1), rasteriser (1)

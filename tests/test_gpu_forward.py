@@ -32,6 +32,20 @@ def check_views(scene, cams, oracle_lib, **cfg):
     return r, out
 
 
+def test_small_scene_matches_stored_oracle_values():
+    """The CUDA image of the 64x64 scene against the oracle values stored under
+    tests/golden (written from the oracle alone), at the stored pixels."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "small_uniform_64x64.txt")
+    a = np.loadtxt(path, comments="#")
+    pix = a[:, :2].astype(np.int64)
+    orc = dict(rgb=a[:, 2:5], T=a[:, 5], flags=a[:, 6].astype(np.int32))
+    scene, cams = scenes.workload_small()
+    _, _, rgb, T, _ = gpu_render(scene, cams)
+    idx = pix[:, 1] * 64 + pix[:, 0]
+    assert_parity(compare(rgb[idx], T[idx], orc))
+
+
 def test_small_uniform_scene(oracle_lib):
     """1 view 64x64, 1,000 primitives, SH degree 0: the small workload, full image."""
     scene, cams = scenes.workload_small()

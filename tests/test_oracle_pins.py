@@ -466,3 +466,22 @@ def test_mip_limits(oracle_lib):
     ok = (i2[:, 0] != 1) & (i2[:, 0] != 4)
     assert np.all(i2[ok, 7] <= i1[ok, 7] * (1 + 1e-12))
     assert np.any(i2[ok, 7] < 0.9 * i1[ok, 7])
+
+
+def load_golden_small():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "small_uniform_64x64.txt")
+    a = np.loadtxt(path, comments="#")
+    return a[:, :2].astype(np.int32), a[:, 2:5], a[:, 5], a[:, 6].astype(np.int32)
+
+
+def test_golden_small_scene_regression(oracle_lib):
+    """The stored oracle image of the 64x64 scene (tests/golden, written by make_golden.py
+    from the oracle alone) is reproduced: a regression guard on the oracle, not a pin."""
+    from paper_2503_18682_gb300 import scenes
+    pix, rgb, T, flags = load_golden_small()
+    scene, cams = scenes.workload_small()
+    out = oracle_lib.render(scene, cams[0], pixels=pix)
+    np.testing.assert_allclose(out["rgb"], rgb, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out["T"], T, rtol=0, atol=1e-12)
+    assert np.array_equal(out["flags"].astype(np.int32), flags)
