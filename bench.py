@@ -35,6 +35,24 @@ WORKLOAD = ("stereo-VR batch: 3M blob primitives (10% axis ratio > 1e3), 16 view
 
 # algorithmic FP32 flops of the rasteriser (FMA = 2): per evaluated (pixel, primitive) pair
 # and extra per composited pair; see the design notes
+# DRAM bytes (read + write) of one full-size rasteriser launch on the stereo batch, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/render_kernel_*),
+# keyed by tile shape and a digest of the rasteriser's sources: a kernel changed since the
+# capture reports null.
+RENDER_TRAFFIC = {("16x16", "661283ceb2654070"): 1.06e9 + 891.32e6}
+RENDER_SOURCES = ("render.cu", "raster_math.cuh", "raygs_internal.cuh")
+
+
+def render_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2503_18682_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 FLOP_EVAL = 17
 FLOP_COMP = 15
 
@@ -353,7 +371,8 @@ def run_ours(args, world, rank, local):
                     preprocess_hbm_frac=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"]),
         autotune=tuned,
         roofline=dict(bound="alu", kernel=f"render_kernel<{r.cfg.tile_w},{r.cfg.tile_h}>", achieved=ach_tf, peak=peak_tf,
-                      unit="TFLOP/s", frac=ach_tf / peak_tf, traffic=None,
+                      unit="TFLOP/s", frac=ach_tf / peak_tf,
+                      traffic=RENDER_TRAFFIC.get((f"{r.cfg.tile_w}x{r.cfg.tile_h}", render_source_digest())),
                       peak_note=f"FP32 {sms} SMs x 128 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz (derived)",
                       algorithmic=f"{FLOP_EVAL} flop per evaluated pair + {FLOP_COMP} per composited pair"),
         clocks=clocks,
