@@ -28,6 +28,16 @@ struct StageOut {
   float dc0, dc1, M00, M01, M11, rho, det;
 };
 
+// A sphere of radius rad around mu lies entirely outside one of the four side planes of
+// the view's frustum (through the outermost pixel-centre rays).
+template <typename T>
+__device__ __forceinline__ bool outside_frustum(const T mu[3], T rad, const DevCam &cam) {
+  return mu[0] - T(cam.xmin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.xmin) * T(cam.xmin)) ||
+         T(cam.xmax) * mu[2] - mu[0] < -rad * t_sqrt(T(1) + T(cam.xmax) * T(cam.xmax)) ||
+         mu[1] - T(cam.ymin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.ymin) * T(cam.ymin)) ||
+         T(cam.ymax) * mu[2] - mu[1] < -rad * t_sqrt(T(1) + T(cam.ymax) * T(cam.ymax));
+}
+
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
 // rotation; s: scales; o: prior opacity.  Returns false when the primitive is skipped or
 // covers no pixel of this view.
@@ -72,10 +82,7 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   {
     T smax = fmax(fmax(s[0], s[1]), s[2]);
     T rad = t_sqrt(kappa) * smax * T(1.001) + T(1e-6);
-    if (mu[0] - T(cam.xmin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.xmin) * T(cam.xmin))) return false;
-    if (T(cam.xmax) * mu[2] - mu[0] < -rad * t_sqrt(T(1) + T(cam.xmax) * T(cam.xmax))) return false;
-    if (mu[1] - T(cam.ymin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.ymin) * T(cam.ymin))) return false;
-    if (T(cam.ymax) * mu[2] - mu[1] < -rad * t_sqrt(T(1) + T(cam.ymax) * T(cam.ymax))) return false;
+    if (outside_frustum<T>(mu, rad, cam)) return false;
   }
 
   // Sec. 3.2 Eq. c: c^2 = mu^T Sigma^-1 mu = |S^-1 R^T mu|^2; skip when c^2 <= kappa.
@@ -281,6 +288,13 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   P.depth_key[idx] = __float_as_uint(z);
 }
 
+// Two passes per chunk of kViewChunk views, so that the expensive stage runs on dense
+// work: a cheap conservative cull of every (primitive, view) pair (near plane, and the
+// frustum test with the largest support radius the pair can have), compacting the
+// survivors per warp into a shared list in primitive order; then one thread per listed
+// pair for the full stage, whose own tests decide.
+constexpr int kViewChunk = 16;
+
 template <int DEG>
 __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) {
   constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
@@ -290,6 +304,14 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   __shared__ float s_q[kPrepThreads * 4];
   __shared__ float s_logit[kPrepThreads];
   __shared__ float s_sh[kPrepThreads * SHP];
+  __shared__ float s_R[kPrepThreads * 9];   // rotation of each primitive
+  __shared__ float s_s[kPrepThreads * 3];   // scales
+  __shared__ float s_o[kPrepThreads];       // prior opacity
+  __shared__ float s_rad[kPrepThreads];     // sqrt(kappa) s_max (0: cull in every view)
+  __shared__ float s_s2max[kPrepThreads];   // s_max^2
+  __shared__ uint8_t s_deg[kPrepThreads];
+  __shared__ uint16_t s_list[kPrepThreads * kViewChunk];
+  __shared__ int s_n;
   extern __shared__ DevCam s_cams[];
 
   const int g0 = blockIdx.x * kPrepThreads;
@@ -303,55 +325,108 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, 1);
   __syncthreads();
 
+  // per-primitive constants
   const int t = threadIdx.x;
-  if (t >= nb) return;
+  const int lane = t & 31, warp = t >> 5;
   const int g = g0 + t;
-  const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
-  const float l0 = s_ls[3 * t], l1 = s_ls[3 * t + 1], l2 = s_ls[3 * t + 2];
-  const float qw = s_q[4 * t], qx = s_q[4 * t + 1], qy = s_q[4 * t + 2], qz = s_q[4 * t + 3];
-  const float logit = s_logit[t];
-  const float *coef = s_sh + t * SHP;
-
-  bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(l0) && isfinite(l1) &&
-                isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
-                isfinite(logit) && (qw * qw + qx * qx + qy * qy + qz * qz > 0.f);
-  bool degenerate = false;
-  if (finite && P.fp64_degenerate) {
-    float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
-    degenerate = (lmax - lmin) > logf(P.degenerate_ratio);
-  }
-  if (!finite) {
-    atomicAdd(&P.counters->n_nonfinite, 1ull);
-    for (int v = 0; v < P.n_views; ++v) P.depth_key[int64_t(v) * P.n + g] = kCulled;
-    return;
-  }
-  float Rp[9];
-  quat_rot<float>(qw, qx, qy, qz, Rp);
-  const float s[3] = {expf(l0), expf(l1), expf(l2)};
-  const float o = 1.f / (1.f + expf(-logit));
-
-  for (int v = 0; v < P.n_views; ++v) {
-    const DevCam &cam = s_cams[v];
-    const int64_t idx = int64_t(v) * P.n + g;
-    float z = depth_f32(cam, mx, my, mz);
-    if (!(z > cam.near_z)) { P.depth_key[idx] = kCulled; continue; }
-    df muc[3];
-    mean_cam_df(cam, mx, my, mz, muc);
-    const float mu[3] = {muc[0].hi, muc[1].hi, muc[2].hi};
-    StageOut so;
-    if (!view_stage<float>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
-      P.depth_key[idx] = kCulled;
-      continue;
+  if (t < nb) {
+    const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
+    const float l0 = s_ls[3 * t], l1 = s_ls[3 * t + 1], l2 = s_ls[3 * t + 2];
+    const float qw = s_q[4 * t], qx = s_q[4 * t + 1], qy = s_q[4 * t + 2], qz = s_q[4 * t + 3];
+    const float logit = s_logit[t];
+    const bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(l0) && isfinite(l1) &&
+                        isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
+                        isfinite(logit) && (qw * qw + qx * qx + qy * qy + qz * qz > 0.f);
+    bool degenerate = false;
+    if (finite && P.fp64_degenerate) {
+      const float lmax = fmaxf(fmaxf(l0, l1), l2), lmin = fminf(fminf(l0, l1), l2);
+      degenerate = (lmax - lmin) > logf(P.degenerate_ratio);
     }
-    float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
-    float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float rgb[3];
-    sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
-    write_record(P, idx, cam, muc, so, rgb, z);
-    if (degenerate && (P.fp64_degenerate == 2 || so.illcond)) {
-      uint32_t slot = atomicAdd(P.deg_count, 1u);
-      P.deg_list[slot] = uint32_t(idx);
+    s_deg[t] = degenerate ? 1 : 0;
+    s_rad[t] = 0.f;
+    if (!finite) {
+      atomicAdd(&P.counters->n_nonfinite, 1ull);
+    } else {
+      quat_rot<float>(qw, qx, qy, qz, &s_R[9 * t]);
+      const float s0 = expf(l0), s1 = expf(l1), s2 = expf(l2);
+      s_s[3 * t] = s0; s_s[3 * t + 1] = s1; s_s[3 * t + 2] = s2;
+      const float o = 1.f / (1.f + expf(-logit));
+      s_o[t] = o;
+      // kappa of the unmodulated opacity bounds every view's (the MIP factor is <= 1)
+      const float kappa0 = 2.f * logf(o / P.p_min);
+      const float smax = fmaxf(fmaxf(s0, s1), s2);
+      s_s2max[t] = smax * smax;
+      s_rad[t] = kappa0 > 0.f ? sqrtf(kappa0) : -1.f;  // < 0: culled everywhere
     }
+  }
+
+  for (int v0 = 0; v0 < P.n_views; v0 += kViewChunk) {
+    const int v1 = min(P.n_views, v0 + kViewChunk);
+    if (t == 0) s_n = 0;
+    __syncthreads();
+    // pass 1: cheap cull, view by view, warp-compacted in primitive order
+    for (int v = v0; v < v1; ++v) {
+      bool keep = false;
+      if (t < nb) {
+        const float sk = s_rad[t];
+        const int64_t idx = int64_t(v) * P.n + g;
+        if (sk > 0.f) {
+          const DevCam &cam = s_cams[v];
+          const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
+          const float z = depth_f32(cam, mx, my, mz);
+          if (z > cam.near_z) {
+            df muc[3];
+            mean_cam_df(cam, mx, my, mz, muc);
+            const float mu[3] = {muc[0].hi, muc[1].hi, muc[2].hi};
+            float s2 = s_s2max[t];
+            if (cam.mip)
+              s2 += P.mip_sigma2 * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) / (cam.fx * cam.fy);
+            const float rad = sk * sqrtf(s2) * 1.01f + 1e-5f * (fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2])) + 1e-5f;
+            keep = !outside_frustum<float>(mu, rad, cam);
+          }
+        }
+        if (!keep) P.depth_key[idx] = kCulled;
+      }
+      const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+      int base = 0;
+      if (lane == 0 && ball) base = atomicAdd(&s_n, __popc(ball));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) s_list[base + __popc(ball & ((1u << lane) - 1u))] = uint16_t(t | ((v - v0) << 8));
+    }
+    (void)warp;
+    __syncthreads();
+    // pass 2: the full stage on the listed pairs
+    const int n_items = s_n;
+    for (int j = t; j < n_items; j += kPrepThreads) {
+      const int tt = s_list[j] & 0xFF, v = v0 + (s_list[j] >> 8);
+      const int gg = g0 + tt;
+      const int64_t idx = int64_t(v) * P.n + gg;
+      const DevCam &cam = s_cams[v];
+      const float mx = s_means[3 * tt], my = s_means[3 * tt + 1], mz = s_means[3 * tt + 2];
+      const float z = depth_f32(cam, mx, my, mz);
+      df muc[3];
+      mean_cam_df(cam, mx, my, mz, muc);
+      const float mu[3] = {muc[0].hi, muc[1].hi, muc[2].hi};
+      const float sv[3] = {s_s[3 * tt], s_s[3 * tt + 1], s_s[3 * tt + 2]};
+      float Rp[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rp[k] = s_R[9 * tt + k];
+      StageOut so;
+      if (!view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+        P.depth_key[idx] = kCulled;
+        continue;
+      }
+      const float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
+      const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+      float rgb[3];
+      sh_colour<DEG>(s_sh + tt * SHP, dx * dn, dy * dn, dz * dn, rgb);
+      write_record(P, idx, cam, muc, so, rgb, z);
+      if (s_deg[tt] && (P.fp64_degenerate == 2 || so.illcond)) {
+        const uint32_t slot = atomicAdd(P.deg_count, 1u);
+        P.deg_list[slot] = uint32_t(idx);
+      }
+    }
+    __syncthreads();
   }
 }
 
