@@ -102,8 +102,10 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
       const float4 A = s_A[j], B = s_B[j];
       const float4 Cc = s_C[j];
       if (COUNT) n_eval += __popc(alive);
-      // the instrumented variant tests every pixel, so its image checks the filter
-      if (!COUNT && !row_may_hit<PX>(A, B, Cc, s_D[j].w, fl_x, fl_y, step)) continue;
+      // with 8 pixels per thread a conservative segment test pays for itself (fewer
+      // pixels per thread are cheaper to test directly); the instrumented variant tests
+      // every pixel, so its image checks the filter
+      if (PX >= 8 && !COUNT && !row_may_hit<PX>(A, B, Cc, s_D[j].w, fl_x, fl_y, step)) continue;
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
       uint32_t hit = eval_pixels<PX>(A, B, Cc.x, fl_x, fl_y, step, q, r, y0, y1, y2);
       hit &= alive;
