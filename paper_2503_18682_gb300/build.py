@@ -29,9 +29,11 @@ def _flags():
 
 
 # Per-file flags.  The vertex stage feeds only float32 records, conservative bounds with
-# explicit margins and an FMA-chain depth key, so its single-precision divisions and square
+# explicit margins and an FMA-chain depth key, and binning's float math only bounds supports
+# with relative margins far above 2 ulp, so their single-precision divisions and square
 # roots may round to within 2 ulp instead of exactly (the FP64 path is unaffected).
-FILE_FLAGS = {"preprocess.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+FILE_FLAGS = {"preprocess.cu": ["-prec-div=false", "-prec-sqrt=false"],
+              "binning.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _compile(src: str, verbose: bool) -> str:
