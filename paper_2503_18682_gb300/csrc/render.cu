@@ -23,9 +23,9 @@
 namespace raygs {
 
 template <int TW, int TH, int PX, bool COUNT>
-__global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
+__global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P) {
   constexpr int NT = TW * TH / PX;  // threads
-  constexpr int NB = 2 * NT;        // records per batch
+  constexpr int NB = NT;            // records per batch
   constexpr int QX = TW / PX;       // threads per tile row
   __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
   __shared__ Rec s_raw[NB];
@@ -115,11 +115,11 @@ __global__ void __launch_bounds__(TW *TH / PX) render_kernel(RenderParams P) {
         for (int k = 0; k < PX; ++k) {
           if (hit & (1u << k)) {
             const float al = fminf(P.alpha_max, pixel_opacity(Cc, q[k], r[k]));
-            const float Tn = T[k] * (1.f - al);
+            const float w = al * T[k];
+            const float Tn = T[k] - w;
             if (Tn < P.t_stop) {
               alive &= ~(1u << k);
             } else {
-              const float w = al * T[k];
               C0[k] = fmaf(w, Dd.x, C0[k]);
               C1[k] = fmaf(w, Dd.y, C1[k]);
               C2[k] = fmaf(w, Dd.z, C2[k]);
