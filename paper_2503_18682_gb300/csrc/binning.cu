@@ -571,52 +571,73 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
       s_pair[j] = R.pairs[p_lo + j];
     }
     __syncthreads();
-    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      int a = 0, b = np - 1;
-      while (a < b) {
-        int m = (a + b + 1) >> 1;
-        if (s_off[m] <= e) a = m; else b = m - 1;
-      }
-      const uint32_t pair = s_pair[a];
-      const uint2 r = R.rect[pair];
-      const uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF;
-      const uint32_t ty = ty0 + (e - s_off[a]);
-      uint32_t xa_t = tx0, xb_t = tx1;
-      const Ell el = R.ell[pair];
-      bool empty = false;
-      const DevCam &cam = R.cams[pair / uint32_t(R.n)];
-      const float ya = float(ty * R.tile_h) + 0.5f;
-      const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
-      if (el.rho < 0.f) {
-        const Rec rc = R.rec[pair];
-        int a0, b0;
-        if (!support_tile_span(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), a0, b0)) {
-          empty = true;
-        } else {
-          xa_t = uint32_t(a0);
-          xb_t = uint32_t(b0);
+    // two rows per thread at a time: both pair look-ups and their loads are issued before
+    // either row's arithmetic
+    for (uint32_t e_base = e0; e_base < e1; e_base += 2 * blockDim.x) {
+      uint32_t ee[2];
+      int aa[2];
+      uint2 rr[2];
+      Ell el2[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        ee[u] = e_base + u * blockDim.x + threadIdx.x;
+        int a = 0, b = np - 1;
+        const uint32_t e = min(ee[u], e1 - 1);
+        while (a < b) {
+          int m = (a + b + 1) >> 1;
+          if (s_off[m] <= e) a = m; else b = m - 1;
         }
-      } else {
-        float xa, xb;
-        if (!ellipse_band(el, ya - 0.02f, yb + 0.02f, xa, xb)) {
-          empty = true;
-        } else {
-          // pixel centres i + 0.5 in [xa, xb] (with a margin), as tile columns
-          const float fa = ceilf(fminf(fmaxf(xa - 0.52f, -1.f), 65536.f * R.tile_w));
-          const float fb = floorf(fminf(fmaxf(xb - 0.48f, -1.f), 65536.f * R.tile_w));
-          if (fa > fb || fb < 0.f) {
+        aa[u] = a;
+        const uint32_t pair = s_pair[a];
+        rr[u] = __ldg(&R.rect[pair]);
+        el2[u] = R.ell[pair];
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t e = ee[u];
+        if (e >= e1) break;
+        const int a = aa[u];
+        const uint32_t pair = s_pair[a];
+        const uint2 r = rr[u];
+        const uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF;
+        const uint32_t ty = ty0 + (e - s_off[a]);
+        uint32_t xa_t = tx0, xb_t = tx1;
+        const Ell &el = el2[u];
+        bool empty = false;
+        const DevCam &cam = R.cams[pair / uint32_t(R.n)];
+        const float ya = float(ty * R.tile_h) + 0.5f;
+        const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
+        if (el.rho < 0.f) {
+          const Rec rc = R.rec[pair];
+          int a0, b0;
+          if (!support_tile_span(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), a0, b0)) {
             empty = true;
           } else {
-            const uint32_t ia = uint32_t(fmaxf(fa, 0.f)), ib = uint32_t(fb);
-            xa_t = max(tx0, ia / uint32_t(R.tile_w));
-            xb_t = min(tx1, ib / uint32_t(R.tile_w));
-            if (xa_t > xb_t) empty = true;
+            xa_t = uint32_t(a0);
+            xb_t = uint32_t(b0);
+          }
+        } else {
+          float xa, xb;
+          if (!ellipse_band(el, ya - 0.02f, yb + 0.02f, xa, xb)) {
+            empty = true;
+          } else {
+            // pixel centres i + 0.5 in [xa, xb] (with a margin), as tile columns
+            const float fa = ceilf(fminf(fmaxf(xa - 0.52f, -1.f), 65536.f * R.tile_w));
+            const float fb = floorf(fminf(fmaxf(xb - 0.48f, -1.f), 65536.f * R.tile_w));
+            if (fa > fb || fb < 0.f) {
+              empty = true;
+            } else {
+              const uint32_t ia = uint32_t(fmaxf(fa, 0.f)), ib = uint32_t(fb);
+              xa_t = max(tx0, ia / uint32_t(R.tile_w));
+              xb_t = min(tx1, ib / uint32_t(R.tile_w));
+              if (xa_t > xb_t) empty = true;
+            }
           }
         }
+        R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
+        R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
+        R.row_key[e] = empty ? kCulled : uint32_t(cam.trow_base) + ty;
       }
-      R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
-      R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
-      R.row_key[e] = empty ? kCulled : uint32_t(cam.trow_base) + ty;
     }
     __syncthreads();
   }

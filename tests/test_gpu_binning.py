@@ -220,3 +220,26 @@ def test_rects_match_oracle_quad(oracle_lib):
         assert inside or near_edge, (g, got, want)
         checked += 1
     assert checked > 500
+
+
+def test_many_tile_rows_keep_order_and_parity(oracle_lib):
+    """More tile rows than the row sort keeps in shared memory (64 tall narrow views at 8x8
+    tiles: 64 x 200 = 12,800 tile rows): the row counters then live in the histogram itself.
+    Tile lists stay in depth order, the ranges partition the instances, and sampled pixels
+    of several views keep oracle parity."""
+    scene = scenes.uniform_scene(3000, seed=41)
+    rng = np.random.default_rng(41)
+    cams = []
+    for _ in range(64):
+        R1, t1 = scenes.look_at(rng.uniform(-0.5, 0.5, 3) * [1, 1, 0] + [0, 0, -0.5], [0.0, 0.0, 3.0])
+        cams.append(scenes.make_camera(8, 1600, 400.0, 400.0, R=R1, t=t1))
+    r, _, rgb, T, nc = gpu_render(scene, cams, tile_w=8, tile_h=8)
+    assert sum(-(-c["height"] // 8) for c in cams) > 12288
+    g_tiles, g_pos = instance_lists(r, r.last_counters["n_instances"])
+    same = np.diff(g_tiles) == 0
+    assert np.all(np.diff(g_pos)[same] > 0)
+    for v in (0, 31, 63):
+        sl = view_slice(r, v)
+        pix, idx = sample_pixels(cams[v], 300, seed=v)
+        orc = oracle_lib.render(scene, cams[v], pixels=pix)
+        assert_parity(compare(rgb[sl][idx], T[sl][idx], orc))
