@@ -260,7 +260,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
       uint32_t k = s_keys[j];
       uint32_t d = (k >> p.shift) & (R - 1);
       uint32_t dst = s_base[d] + j - s_tpre[d];
-      p.keys_out[dst] = k;
+      uint32_t kout = k;
+      if constexpr (!WIDE) {
+        if (p.row_rect) {
+          const uint2 r = p.row_rect[s_vals[j]];
+          kout = (r.y >> 16) - (r.x >> 16) + 1;
+        }
+      }
+      p.keys_out[dst] = kout;
       SortVal<WIDE>::store(p, dst, s_vals[j]);
     }
     __syncthreads();
@@ -409,26 +416,12 @@ cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ pair -> tile rows
-__global__ void __launch_bounds__(256) count_rows_kernel(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt,
-                                                         const Counters *c) {
-  const uint32_t n = c->n_visible;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    uint2 r = rect[pairs[p]];
-    cnt[p] = (r.y >> 16) - (r.x >> 16) + 1;
-  }
-}
-
-cudaError_t launch_count_rows(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt, const Counters *c, int G,
-                              cudaStream_t st) {
-  count_rows_kernel<<<G, 256, 0, st>>>(pairs, rect, cnt, c);
-  return cudaGetLastError();
-}
 
 // Pixel-centre columns of the band ya <= y <= yb (pixel-centre rows) inside the ellipse.
 // The right boundary x_r(y) is concave with its maximum at the rightmost point of the
 // ellipse, the left one convex: clamping that point's y into the band gives the extremes.
 __device__ __forceinline__ bool ellipse_band(const Ell &e, float ya, float yb, float &xa, float &xb) {
-  const float rho = e.rho * 1.001f + 1e-6f;
+  const float rho = 1.001f;
   const float hy = sqrtf(rho * e.a / e.det);
   const float lo = fmaxf(ya - e.cy, -hy), hi = fminf(yb - e.cy, hy);
   if (lo > hi) return false;
@@ -576,7 +569,6 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
     for (uint32_t e_base = e0; e_base < e1; e_base += 2 * blockDim.x) {
       uint32_t ee[2];
       int aa[2];
-      uint2 rr[2];
       Ell el2[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -589,7 +581,6 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
         }
         aa[u] = a;
         const uint32_t pair = s_pair[a];
-        rr[u] = __ldg(&R.rect[pair]);
         el2[u] = R.ell[pair];
       }
 #pragma unroll
@@ -598,16 +589,15 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
         if (e >= e1) break;
         const int a = aa[u];
         const uint32_t pair = s_pair[a];
-        const uint2 r = rr[u];
-        const uint32_t tx0 = r.x & 0xFFFF, ty0 = r.x >> 16, tx1 = r.y & 0xFFFF;
+        const Ell &el = el2[u];
+        const uint32_t tx0 = el.r0 & 0xFFFF, ty0 = el.r0 >> 16, tx1 = el.r1 & 0xFFFF;
         const uint32_t ty = ty0 + (e - s_off[a]);
         uint32_t xa_t = tx0, xb_t = tx1;
-        const Ell &el = el2[u];
         bool empty = false;
         const DevCam &cam = R.cams[pair / uint32_t(R.n)];
         const float ya = float(ty * R.tile_h) + 0.5f;
         const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
-        if (el.rho < 0.f) {
+        if (!(el.a > 0.f)) {
           const Rec rc = R.rec[pair];
           int a0, b0;
           if (!support_tile_span(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), a0, b0)) {

@@ -87,7 +87,6 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.ell = take(sizeof(Ell) * VN);
   L.rec = take(sizeof(Rec) * VN);
   for (int i = 0; i < 2; ++i) { L.s1k[i] = take(4 * VN); L.s1v[i] = take(4 * VN); }
-  L.cnt = take(4 * VN);
   L.off = take(4 * VN);
   L.partial = take(4 * size_t(G));
   L.rtstart_len = uint32_t(C / kEmitTile + 2);
@@ -185,16 +184,15 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
     sp.hist = hist;
     sp.G = w.G;
     sp.d_total = pass == 0 ? &ctr->n_visible : nullptr;
+    sp.row_rect = pass == 3 ? w.at<uint2>(w.L.rect) : nullptr;
     if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
     cur = dst;
   }
   w.s1_final = cur;
   const uint32_t *pairs = w.at<uint32_t>(w.L.s1v[cur]);
   // 2a. pairs -> tile rows
-  if ((e = launch_count_rows(pairs, w.at<uint2>(w.L.rect), w.at<uint32_t>(w.L.cnt), ctr, w.G, st)) != cudaSuccess)
-    return e;
   ScanJob J{};
-  J.cnt = w.at<uint32_t>(w.L.cnt);
+  J.cnt = w.at<uint32_t>(w.L.s1k[cur]);  // the last depth pass left each pair's row count here
   J.off = w.at<uint32_t>(w.L.off);
   J.d_n = &ctr->n_visible;
   J.partial = w.at<uint32_t>(w.L.partial);

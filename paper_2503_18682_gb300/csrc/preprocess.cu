@@ -181,13 +181,14 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
     const T M11 = kpt * (g01 * g01 + g11 * g11) - hh1 * hh1;
     const T det = M00 * M11 - M01 * M01;
     out.rho = -1.f;
+    out.M00 = -1.f;  // no bounded ellipse unless set below
     if (M00 > T(0) && M11 > T(0) && det > T(1e-4) * M00 * M11) {
       const T dc0 = (M11 * hh0 - M01 * hh1) / det, dc1 = (M00 * hh1 - M01 * hh0) / det;
       const T rho = T(1) + hh0 * dc0 + hh1 * dc1;
       if (rho > T(0)) {
         out.dc0 = float(dc0); out.dc1 = float(dc1);
-        out.M00 = float(M00); out.M01 = float(M01); out.M11 = float(M11);
-        out.rho = float(rho); out.det = float(det);
+        out.M00 = float(M00 / rho); out.M01 = float(M01 / rho); out.M11 = float(M11 / rho);
+        out.rho = float(rho); out.det = float(det / (rho * rho));
         // a bounded support ellipse bounds the pixels even where the quad reaches
         // behind the camera
         const T ucx = T(cam.fx) * mu[0] / mu[2] + T(cam.cx) + dc0;
@@ -280,10 +281,11 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
                            uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
   Ell e;
+  e.r0 = uint32_t(so.tx0) | (uint32_t(so.ty0) << 16);
+  e.r1 = uint32_t(so.tx1) | (uint32_t(so.ty1) << 16);
   e.cx = u.hi + so.dc0;
   e.cy = v.hi + so.dc1;
-  e.a = so.M00; e.b = so.M01; e.d = so.M11;
-  e.rho = so.rho; e.det = so.det; e.pad = 0.f;
+  e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
   P.ell[idx] = e;
   P.depth_key[idx] = __float_as_uint(z);
 }

@@ -53,13 +53,14 @@ struct Counters {
   uint32_t n_rows_kept;     // support rows with at least one tile
 };
 
-// Screen-space support ellipse of a (primitive, view): pixel centres p with
-// (p - c)^T [[a, b], [b, d]] (p - c) <= rho are exactly the rays with D <= kappa (up to
-// rounding).  rho < 0 marks a support that is not a bounded ellipse in the image (or is
-// too ill-conditioned in float32): binning then keeps the whole rectangle.
-struct __align__(16) Ell {
-  float cx, cy, a, b;
-  float d, rho, det, pad;
+// Screen-space support of a (primitive, view), one 32-byte sector for the tile-row pass:
+// its tile rectangle (as in the rect array) and the ellipse of pixel centres p with
+// (p - c)^T [[a, b], [b, d]] (p - c) <= 1 that holds exactly the rays with D <= kappa (up to
+// rounding), det = ad - b^2.  a < 0 marks a support that is not a bounded ellipse in the
+// image (or is too ill-conditioned in float32): binning then bounds it tile by tile.
+struct __align__(32) Ell {
+  uint32_t r0, r1;  // tx0 | ty0 << 16, tx1 | ty1 << 16
+  float cx, cy, a, b, d, det;
 };
 
 struct RasterCfg {
@@ -183,6 +184,9 @@ struct SortPass {
   uint2 *wvals_out;
   const uint2 *seg;
   const uint32_t *seg_len;
+  // when set, the pass writes each item's tile-row count (from its pair's rectangle) in
+  // place of its key (the last depth pass: the keys are not needed after it)
+  const uint2 *row_rect;
 };
 
 // Exclusive scan of per-unit output counts, with the unit that holds the first output of
@@ -298,8 +302,6 @@ void note_cuda_error(cudaError_t e);
 
 cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st);
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
-cudaError_t launch_count_rows(const uint32_t *pairs, const uint2 *rect, uint32_t *cnt, const Counters *c, int G,
-                              cudaStream_t st);
 cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
@@ -314,7 +316,7 @@ cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], cnt, off, partial, rtstart,
+  size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], off, partial, rtstart,
       seg, seg_len, seg_off, rk[2], rv[2], trange, tcnt, toff, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };

@@ -159,7 +159,7 @@ def test_unbounded_supports_keep_every_covered_tile(oracle_lib, tile):
     r, _, rgb, T, nc = gpu_render(sc, cams, tile_w=tile[0], tile_h=tile[1])
     ell = fetch(r.debug_buffer(7), 8 * n * len(cams), np.float32).reshape(-1, 8)
     order = fetch(r.debug_buffer(3), r.last_counters["n_visible"], np.uint32)
-    unbounded = {int(p) for p in order if ell[p, 5] < 0}
+    unbounded = {int(p) for p in order if not ell[p, 4] > 0}   # (r0, r1, cx, cy, a, b, d, det)
     assert len(unbounded) >= 10, len(unbounded)
     dropped, n_rect, n_kept = assert_dropped_tiles_miss_support(oracle_lib, sc, cams, r, n, tile, unbounded)
     assert dropped > 0 and n_kept < n_rect
