@@ -771,23 +771,17 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
       for (uint32_t t = 0; t < len; ++t) atomicOr(&mask[g * TP + int(xa + t)], 1u << lane);
     }
     __syncthreads();
-    // per tile, a warp scans the group counts (lane g = group g)
+    // per tile (one thread each), the group counts in group order
     uint32_t *other = s_mask + (1 - buf) * VW * TP;
-    for (int x = warp; x < TX; x += NT / 32) {
-      const uint32_t c = lane < VW ? __popc(mask[lane * TP + x]) : 0u;
-      uint32_t inc = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
+    for (int x = threadIdx.x; x < TX; x += NT) {
+      uint32_t run = s_cur[x];
+#pragma unroll 8
+      for (int g = 0; g < VW; ++g) {
+        s_pre[g * TP + x] = run;
+        run += __popc(mask[g * TP + x]);
+        other[g * TP + x] = 0u;
       }
-      const uint32_t run = s_cur[x];
-      if (lane < VW) {
-        s_pre[lane * TP + x] = run + inc - c;
-        other[lane * TP + x] = 0u;
-      }
-      __syncwarp();
-      if (lane == 31) s_cur[x] = run + inc;
+      s_cur[x] = run;
     }
     __syncthreads();
 #pragma unroll
