@@ -549,6 +549,10 @@ __device__ bool support_tile_span(const Rec &r, const DevCam &cam, int tile_w, f
 __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   __shared__ uint32_t s_off[kEmitTile + 1];
   __shared__ uint32_t s_pair[kEmitTile + 1];
+  __shared__ uint32_t s_trow[kTrowsShared];  // this CTA's instances per tile row
+  const bool shared_trows = R.trows <= kTrowsShared;
+  if (shared_trows)
+    for (int i = threadIdx.x; i < R.trows; i += blockDim.x) s_trow[i] = 0u;
   const uint32_t total = R.counters->n_rows_clamped;
   const unsigned long long total_all = R.counters->n_rows;
   const uint32_t nvis = R.counters->n_visible;
@@ -627,10 +631,18 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
         R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
         R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
         R.row_key[e] = empty ? kCulled : uint32_t(cam.trow_base) + ty;
+        if (!empty) {
+          const uint32_t grow = uint32_t(cam.trow_base) + ty, len = xb_t - xa_t + 1;
+          if (shared_trows) atomicAdd(&s_trow[grow], len);
+          else atomicAdd(&R.trow_inst[grow], (unsigned long long)len);
+        }
       }
     }
     __syncthreads();
   }
+  if (shared_trows)
+    for (int i = threadIdx.x; i < R.trows; i += blockDim.x)
+      if (s_trow[i]) atomicAdd(&R.trow_inst[i], (unsigned long long)s_trow[i]);
 }
 
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st) {
@@ -680,39 +692,52 @@ __device__ __forceinline__ const DevCam &view_of_trow(const ExpandParams &E, int
   return E.cams[v];
 }
 
-// Instances per tile of one tile row: each sorted row covers the tile columns
-// [txa, txa + len); a difference array over the columns and its prefix sum count them.
-__global__ void __launch_bounds__(256) tile_count_kernel(ExpandParams E) {
-  extern __shared__ uint32_t s_diff[];  // [tiles_x + 1]
-  __shared__ uint32_t s_ws[33];
-  __shared__ int s_v;
-  const int grow = blockIdx.x;
-  if (threadIdx.x == 0) { int v; view_of_trow(E, grow, v); s_v = v; }
+// Exclusive scan of the per-tile-row instance totals in place (one block; 64-bit running
+// sums): each tile row's first instance, the instance total, its capacity clamp and the
+// overflow flag.
+__global__ void __launch_bounds__(1024) trow_scan_kernel(unsigned long long *v, int n, Counters *c, uint32_t cap) {
+  __shared__ unsigned long long ws[32];
+  const int per = (n + 1023) / 1024;
+  const int b = min(n, int(threadIdx.x) * per), e = min(n, b + per);
+  unsigned long long s = 0;
+  for (int i = b; i < e; ++i) s += v[i];
+  // block exclusive scan of s (warp scans of 64-bit values, then of the warp totals)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
   __syncthreads();
-  const DevCam &cam = E.cams[s_v];
-  const int TX = cam.tiles_x;
-  for (int x = threadIdx.x; x <= TX; x += blockDim.x) s_diff[x] = 0;
-  __syncthreads();
-  const uint2 rr = E.trow_ranges[grow];
-  for (uint32_t i = rr.x + threadIdx.x; i < rr.y; i += blockDim.x) {
-    const uint32_t pk = E.rows[i].y;
-    const uint32_t xa = pk & 0xFFFFu, len = pk >> 16;
-    atomicAdd(&s_diff[xa], 1u);
-    atomicSub(&s_diff[xa + len], 1u);
+  if (warp == 0) {
+    unsigned long long t = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
   }
   __syncthreads();
-  // inclusive prefix of the differences = instances of each tile
-  const int per = (TX + int(blockDim.x) - 1) / int(blockDim.x);
-  const int x0 = min(TX, int(threadIdx.x) * per), x1 = min(TX, x0 + per);
-  uint32_t s = 0;
-  for (int x = x0; x < x1; ++x) s += s_diff[x];
-  uint32_t tot;
-  uint32_t run = block_excl_scan(s, s_ws, &tot);
-  const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
-  for (int x = x0; x < x1; ++x) {
-    run += s_diff[x];
-    E.tile_cnt[tile0 + x] = run;
+  unsigned long long run = (warp ? ws[warp - 1] : 0ull) + x - s;
+  for (int i = b; i < e; ++i) {
+    const unsigned long long t = v[i];
+    v[i] = run;
+    run += t;
   }
+  if (threadIdx.x == 1023) {
+    const unsigned long long total = ws[31];
+    c->n_instances = total;
+    c->n_inst_clamped = total > cap ? cap : uint32_t(total);
+    if (total > cap) c->overflow = 1u;
+  }
+}
+
+cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st) {
+  trow_scan_kernel<<<1, 1024, 0, st>>>(trow_inst, trows, c, cap);
+  return cudaGetLastError();
 }
 
 // Instance lists of one tile row.  Rows are taken in sorted (depth) order, NT * KR at a
@@ -739,13 +764,45 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
-  for (int x = threadIdx.x; x < TX; x += NT) {
-    const uint32_t o = E.tile_off[tile0 + x], c = E.tile_cnt[tile0 + x];
-    s_cur[x] = o;
-    E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + c, E.cap));
-  }
-  for (int j = threadIdx.x; j < 2 * VW * TP; j += NT) s_mask[j] = 0u;
+  // Instances per tile of this tile row: each row covers the tile columns [txa, txa + len);
+  // a difference array over the columns (in the group-prefix buffer) and its prefix sum
+  // count them, and their exclusive scan from the tile row's first instance places them.
   const uint2 rr = E.trow_ranges[grow];
+  uint32_t *s_diff = s_pre;  // TX + 1 words (VW * TP >= TX + 1)
+  for (int x = threadIdx.x; x <= TX; x += NT) s_diff[x] = 0u;
+  __syncthreads();
+  for (uint32_t i = rr.x + threadIdx.x; i < rr.y; i += NT) {
+    const uint32_t pk = E.rows[i].y;
+    const uint32_t xa = pk & 0xFFFFu, len = pk >> 16;
+    atomicAdd(&s_diff[xa], 1u);
+    atomicSub(&s_diff[xa + len], 1u);
+  }
+  __syncthreads();
+  {
+    __shared__ uint32_t s_ws[33];
+    const int per = (TX + NT - 1) / NT;
+    const int x0 = min(TX, int(threadIdx.x) * per), x1 = min(TX, x0 + per);
+    uint32_t dsum = 0;
+    for (int x = x0; x < x1; ++x) dsum += s_diff[x];
+    uint32_t dtot;
+    const uint32_t dpre = block_excl_scan(dsum, s_ws, &dtot);  // differences before the chunk
+    uint32_t csum = 0, run = dpre;
+    for (int x = x0; x < x1; ++x) { run += s_diff[x]; csum += run; }
+    __syncthreads();
+    uint32_t ctot;
+    const uint32_t cpre = block_excl_scan(csum, s_ws, &ctot);  // instances before the chunk
+    const unsigned long long base = E.trow_base[grow];
+    uint32_t o = uint32_t(min(base, (unsigned long long)E.cap)) + cpre;
+    run = dpre;
+    for (int x = x0; x < x1; ++x) {
+      run += s_diff[x];  // this tile's instance count
+      s_cur[x] = o;
+      E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + run, E.cap));
+      o += run;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 2 * VW * TP; j += NT) s_mask[j] = 0u;
   constexpr uint32_t STEP = uint32_t(NT) * KR;
   uint2 nxt[KR];
   auto load_rows = [&](uint32_t base) {
@@ -803,11 +860,6 @@ size_t expand_smem(int max_tiles_x) {
   return sizeof(uint32_t) * size_t(max_tiles_x + 1) * size_t(1 + 3 * (NT / 32) * KR);
 }
 
-cudaError_t launch_tile_counts(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {
-  if (n_trows == 0) return cudaSuccess;
-  tile_count_kernel<<<n_trows, 256, sizeof(uint32_t) * size_t(max_tiles_x + 1), st>>>(E);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {
   if (n_trows == 0) return cudaSuccess;

@@ -98,8 +98,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   for (int i = 0; i < 2; ++i) { L.rk[i] = take(4 * C + 16); L.rv[i] = take(8 * C + 16); }
   L.inst = take(4 * C + 16);
   L.trange = take(8 * size_t(trows) + 16);
-  L.tcnt = take(4 * size_t(tiles) + 16);
-  L.toff = take(4 * size_t(tiles) + 16);
+  L.trinst = take(8 * size_t(trows) + 16);
   L.hist = take(4 * 512 * size_t(G) + 4 * (512 * size_t(G) / 2048 + 1));
   L.ranges = take(8 * size_t(tiles));
   L.deg = take(4 * VN);
@@ -219,6 +218,10 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   R.seg = w.at<uint2>(w.L.seg);
   R.seg_len = w.at<uint32_t>(w.L.seg_len);
   R.row_key = w.at<uint32_t>(w.L.rk[0]);
+  R.trow_inst = w.at<unsigned long long>(w.L.trinst);
+  R.trows = int(w.trows);
+  if ((e = cudaMemsetAsync(R.trow_inst, 0, sizeof(unsigned long long) * size_t(w.trows), st)) != cudaSuccess)
+    return e;
   if ((e = launch_rows(R, w.G, st)) != cudaSuccess) return e;
   ScanJob J2{};
   J2.cnt = R.seg_len;
@@ -231,7 +234,11 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   J2.d_total_clamped = &ctr->n_inst_clamped;
   J2.cap = cap;
   J2.d_overflow = &ctr->overflow;
-  if ((e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
+  // the emission offsets only index the backward's partials
+  const bool emission = w.cfg.enable_backward != 0;
+  if (emission && (e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
+  // first instance of every tile row, the instance total and the capacity check
+  if ((e = launch_trow_scan(R.trow_inst, int(w.trows), ctr, cap, st)) != cudaSuccess) return e;
   // 3. stable sort of the non-empty rows by global tile row (8-bit digits); the first
   // pass drops the empty rows and gathers each row's payload
   const int rbits = tile_sort_bits(w.trows);
@@ -270,25 +277,10 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   X.n_views = w.n_views;
   X.trow_ranges = trange;
   X.rows = w.at<uint2>(w.L.rv[cur]);
-  X.tile_cnt = w.at<uint32_t>(w.L.tcnt);
-  X.tile_off = w.at<uint32_t>(w.L.toff);
+  X.trow_base = R.trow_inst;
   X.ranges = w.at<uint2>(w.L.ranges);
   X.inst = w.at<uint32_t>(w.L.inst);
   X.cap = cap;
-  if ((e = launch_tile_counts(X, int(w.trows), w.max_tiles_x, st)) != cudaSuccess) return e;
-  ScanJob J3{};
-  J3.cnt = X.tile_cnt;
-  J3.off = w.at<uint32_t>(w.L.toff);
-  J3.d_n = nullptr;
-  J3.n_static = uint32_t(w.tiles);
-  J3.partial = w.at<uint32_t>(w.L.partial);
-  J3.tile_start = nullptr;
-  J3.tstart_len = 0;
-  J3.d_total = w.at<unsigned long long>(w.L.tscan);
-  J3.d_total_clamped = reinterpret_cast<uint32_t *>(w.at<unsigned long long>(w.L.tscan) + 1);
-  J3.cap = cap;
-  J3.d_overflow = &ctr->overflow;
-  if ((e = launch_scan(J3, w.G, st)) != cudaSuccess) return e;
   return launch_expand(X, int(w.trows), w.max_tiles_x, st);
 }
 

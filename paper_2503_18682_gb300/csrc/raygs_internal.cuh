@@ -219,7 +219,10 @@ struct RowsParams {
   uint2 *seg;               // per row: (sorted pair position, ty | txa << 16)
   uint32_t *seg_len;        // per row: tiles of the row inside the support
   uint32_t *row_key;        // per row: global tile row, or kCulled when the run is empty
+  unsigned long long *trow_inst;  // [tile rows] instances of each tile row (accumulated)
+  int trows;
 };
+constexpr int kTrowsShared = 4096;  // tile rows whose instance totals a CTA keeps in shared memory
 
 // Per-tile-row passes over the support rows sorted by tile row (stable, so each tile row
 // lists its rows in depth order): per-tile instance counts, then the instance lists.
@@ -228,8 +231,7 @@ struct ExpandParams {
   int n_views;
   const uint2 *trow_ranges;  // [tile rows] range of the tile row in the sorted rows
   const uint2 *rows;         // sorted rows: (sorted pair position, txa | len << 16)
-  uint32_t *tile_cnt;        // [tiles] instances per tile
-  const uint32_t *tile_off;  // [tiles] exclusive scan of tile_cnt
+  const unsigned long long *trow_base;  // [tile rows] first instance of each tile row
   uint2 *ranges;             // [tiles] instance range of every tile (clamped to cap)
   uint32_t *inst;            // [cap] sorted pair position of every instance
   uint32_t cap;
@@ -305,7 +307,7 @@ cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
 cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
-cudaError_t launch_tile_counts(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
+cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st);
 cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
                           cudaStream_t st);
@@ -317,7 +319,7 @@ cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
   size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], off, partial, rtstart,
-      seg, seg_len, seg_off, rk[2], rv[2], trange, tcnt, toff, inst, hist, ranges, deg, degc, partials, pg, total;
+      seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };
 
