@@ -302,9 +302,14 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
   constexpr int SHP = K3 + 1;  // padded row
   __shared__ float s_means[kPrepThreads * 3];
-  __shared__ float s_ls[kPrepThreads * 3];
-  __shared__ float s_q[kPrepThreads * 4];
-  __shared__ float s_logit[kPrepThreads];
+  // log-scales, quaternions and logits are read once, for the per-primitive constants;
+  // their space then holds the list of (primitive, view) pairs
+  static_assert(kPrepThreads * kViewChunk * sizeof(uint16_t) <= kPrepThreads * 8 * sizeof(float), "list");
+  __shared__ __align__(16) float s_scratch[kPrepThreads * 8];
+  float *s_ls = s_scratch;
+  float *s_q = s_scratch + 3 * kPrepThreads;
+  float *s_logit = s_scratch + 7 * kPrepThreads;
+  uint16_t *s_list = reinterpret_cast<uint16_t *>(s_scratch);
   __shared__ float s_sh[kPrepThreads * SHP];
   __shared__ float s_R[kPrepThreads * 9];   // rotation of each primitive
   __shared__ float s_s[kPrepThreads * 3];   // scales
@@ -312,7 +317,6 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   __shared__ float s_rad[kPrepThreads];     // sqrt(kappa) s_max (0: cull in every view)
   __shared__ float s_s2max[kPrepThreads];   // s_max^2
   __shared__ uint8_t s_deg[kPrepThreads];
-  __shared__ uint16_t s_list[kPrepThreads * kViewChunk];
   __shared__ int s_n;
   extern __shared__ DevCam s_cams[];
 
