@@ -39,7 +39,7 @@ WORKLOAD = ("stereo-VR batch: 3M blob primitives (10% axis ratio > 1e3), 16 view
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/render_kernel_*),
 # keyed by tile shape and a digest of the rasteriser's sources: a kernel changed since the
 # capture reports null.
-RENDER_TRAFFIC = {("16x16", "207dc4c3cc1e7850"): 829.09e6 + 888.82e6}
+RENDER_TRAFFIC = {("16x16/b1", "207dc4c3cc1e7850"): 829.09e6 + 888.82e6}
 RENDER_SOURCES = ("render.cu", "raster_math.cuh", "raygs_internal.cuh")
 
 
@@ -258,7 +258,7 @@ def run_ours(args, world, rank, local):
     else:
         kw = {}
     r = raygs.Renderer(cams, n, device=dev, capacity=tune_cap, **{k: v for k, v in kw.items()
-                                                                  if k in ("tile_w", "tile_h")})
+                                                                  if k in ("tile_w", "tile_h", "batch_records")})
     stream = torch.cuda.Stream(device=dev)
     stream.wait_stream(torch.cuda.current_stream())
     rgb, T, nc = r.alloc_outputs()
@@ -304,7 +304,8 @@ def run_ours(args, world, rank, local):
     # binning.  Every step is still one complete 16-view batch.
     plans = [(r, stream)]
     for _ in range(max(1, args.in_flight) - 1):
-        r2 = raygs.Renderer(cams, n, device=dev, capacity=r.capacity, tile_w=r.cfg.tile_w, tile_h=r.cfg.tile_h)
+        r2 = raygs.Renderer(cams, n, device=dev, capacity=r.capacity, tile_w=r.cfg.tile_w, tile_h=r.cfg.tile_h,
+                            batch_records=r.cfg.batch_records)
         s2 = torch.cuda.Stream(device=dev)
         s2.wait_stream(torch.cuda.current_stream())
         o2 = r2.alloc_outputs()
@@ -387,7 +388,8 @@ def run_ours(args, world, rank, local):
         ms_per_step=ms_max, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic",
         config=dict(workload=WORKLOAD, n_gaussians=n, views=len(cams), pixels=r.num_pixels,
-                    tiles=r.num_tiles, tile=f"{r.cfg.tile_w}x{r.cfg.tile_h}", batches_in_flight=len(plans),
+                    tiles=r.num_tiles, tile=f"{r.cfg.tile_w}x{r.cfg.tile_h}", batch_records=int(r.cfg.batch_records),
+                    batches_in_flight=len(plans),
                     l2="inputs larger than L2 (no flush)", parallelism=f"replica x{world}"),
         stereo_pairs_per_s=4 * value,
         one_batch_at_a_time=dict(value=world / (single_ms / 1e3), ms_per_step=single_ms),
@@ -400,7 +402,8 @@ def run_ours(args, world, rank, local):
         autotune=tuned,
         roofline=dict(bound="alu", kernel=f"render_kernel<{r.cfg.tile_w},{r.cfg.tile_h}>", achieved=ach_tf, peak=peak_tf,
                       unit="TFLOP/s", frac=ach_tf / peak_tf,
-                      traffic=RENDER_TRAFFIC.get((f"{r.cfg.tile_w}x{r.cfg.tile_h}", render_source_digest())),
+                      traffic=RENDER_TRAFFIC.get((f"{r.cfg.tile_w}x{r.cfg.tile_h}/b{r.cfg.batch_records}",
+                                                  render_source_digest())),
                       peak_note=f"FP32 {sms} SMs x 128 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz (derived)",
                       algorithmic=f"{FLOP_EVAL} flop per evaluated pair + {FLOP_COMP} per composited pair"),
         clocks=clocks,

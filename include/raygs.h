@@ -90,6 +90,8 @@ typedef struct {
                               nearly edge-on); 2 in every view where they are visible */
   float degenerate_ratio; /* 1e3 */
   int32_t enable_backward; /* 1: reserve workspace for raygs_render_backward (default 0) */
+  int32_t batch_records;  /* records the rasteriser stages in shared memory per thread and
+                             batch: 1 (default) or 2 */
 } raygs_config;
 
 /* Device-side counters of the last preprocess / bin_sort / render sequence. */
@@ -222,13 +224,14 @@ raygs_status raygs_graph_launch(raygs_plan *plan, void *stream);
 
 /*
  * Autotuner for the batched launch: for every compiled tile shape (16x16, 16x8, 32x16,
- * 8x8 pixels; the shared-memory batch is two records per thread of each shape), build a
- * plan over `workspace` (caller-owned, at least raygs_autotune_workspace_bytes() bytes),
- * run one untimed pass, skip the shape if its instances overflow `max_instances`, then time
- * `iters` passes of preprocess + bin_sort + render with CUDA events on `stream`.  Writes the
- * fastest shape into cfg_inout->tile_w/tile_h and, if ms_out is non-NULL, the mean time per
- * pass of each shape into ms_out[0..3] (-1 when skipped).  Synchronises `stream`.
- * Returns RAYGS_ERR_CAPACITY when no shape fits.  (Not in the paper.)
+ * 8x8 pixels) and shared-memory batch (1 or 2 records per rasteriser thread), in that
+ * order (shape-major), build a plan over `workspace` (caller-owned, at least
+ * raygs_autotune_workspace_bytes() bytes), run one untimed pass, skip the candidate if its
+ * instances overflow `max_instances`, then time `iters` passes of preprocess + bin_sort +
+ * render with CUDA events on `stream`.  Writes the fastest candidate into
+ * cfg_inout->tile_w/tile_h/batch_records and, if ms_out is non-NULL, the mean time per pass
+ * of each candidate into ms_out[0..7] (-1 when skipped).  Synchronises `stream`.
+ * Returns RAYGS_ERR_CAPACITY when no candidate fits.  (Not in the paper.)
  */
 raygs_status raygs_autotune(const raygs_camera *cams, int32_t n_views, const raygs_scene *scene,
                             int64_t max_instances, raygs_config *cfg_inout, void *workspace, size_t bytes,

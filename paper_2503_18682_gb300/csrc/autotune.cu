@@ -1,7 +1,7 @@
 // Launch-configuration autotuner: times the whole hot path (vertex stage, binning,
-// rasteriser) for every compiled tile shape on the caller's own scene and views, in one
-// caller-owned workspace, and keeps the fastest.  Host-side plans only; no device memory
-// is allocated.
+// rasteriser) for every compiled tile shape and rasteriser batch on the caller's own scene
+// and views, in one caller-owned workspace, and keeps the fastest.  Host-side plans only;
+// no device memory is allocated.
 #include <vector>
 
 #include "raygs_internal.cuh"
@@ -11,9 +11,10 @@ using namespace raygs;
 namespace {
 
 struct Candidate {
-  int tw, th;
+  int tw, th, nb;
 };
-constexpr Candidate kCandidates[] = {{16, 16}, {16, 8}, {32, 16}, {8, 8}};
+constexpr Candidate kCandidates[] = {{16, 16, 1}, {16, 16, 2}, {16, 8, 1}, {16, 8, 2},
+                                     {32, 16, 1}, {32, 16, 2}, {8, 8, 1},  {8, 8, 2}};
 constexpr int kNumCandidates = int(sizeof(kCandidates) / sizeof(kCandidates[0]));
 
 }  // namespace
@@ -28,6 +29,7 @@ size_t raygs_autotune_workspace_bytes(const raygs_camera *cams, int32_t n_views,
   for (int c = 0; c < kNumCandidates; ++c) {
     cfg.tile_w = kCandidates[c].tw;
     cfg.tile_h = kCandidates[c].th;
+    cfg.batch_records = kCandidates[c].nb;
     raygs_plan *p = nullptr;
     if (raygs_plan_create(cams, n_views, n_gaussians, max_instances, &cfg, &p) != RAYGS_OK) return 0;
     size_t b = raygs_plan_workspace_bytes(p);
@@ -58,6 +60,7 @@ raygs_status raygs_autotune(const raygs_camera *cams, int32_t n_views, const ray
     if (ms_out) ms_out[c] = -1.f;
     cfg.tile_w = kCandidates[c].tw;
     cfg.tile_h = kCandidates[c].th;
+    cfg.batch_records = kCandidates[c].nb;
     raygs_plan *p = nullptr;
     raygs_status s = raygs_plan_create(cams, n_views, scene->n, max_instances, &cfg, &p);
     if (s != RAYGS_OK) { result = s; break; }
@@ -93,6 +96,7 @@ raygs_status raygs_autotune(const raygs_camera *cams, int32_t n_views, const ray
   if (best < 0) return RAYGS_ERR_CAPACITY;
   cfg_inout->tile_w = kCandidates[best].tw;
   cfg_inout->tile_h = kCandidates[best].th;
+  cfg_inout->batch_records = kCandidates[best].nb;
   return RAYGS_OK;
 }
 

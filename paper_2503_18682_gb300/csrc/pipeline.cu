@@ -35,7 +35,8 @@ bool config_valid(const raygs_config &cfg) {
                        (cfg.tile_w == 32 && cfg.tile_h == 16) || (cfg.tile_w == 8 && cfg.tile_h == 8);
   return tile_ok && cfg.p_min > 0.f && cfg.p_min < 1.f && cfg.t_stop >= 0.f && cfg.t_stop < 1.f &&
          cfg.alpha_max > 0.f && cfg.alpha_max < 1.f && cfg.mip_sigma2 >= 0.f && cfg.degenerate_ratio > 1.f &&
-         cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2 && (cfg.enable_backward == 0 || cfg.enable_backward == 1);
+         cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2 && (cfg.enable_backward == 0 || cfg.enable_backward == 1) &&
+         (cfg.batch_records == 1 || cfg.batch_records == 2);
 }
 
 bool camera_valid(const raygs_camera &c) {
@@ -303,7 +304,7 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
     cudaError_t e = cudaMemsetAsync(P.eval_counts, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
-  return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);
+  return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.cfg.batch_records, w.tiles, count, st);
 }
 
 cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T_final, const int32_t *n_contrib,

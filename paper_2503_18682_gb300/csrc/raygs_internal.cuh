@@ -309,8 +309,8 @@ cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
 cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st);
 cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
-cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
-                          cudaStream_t st);
+cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
+                          bool count, cudaStream_t st);
 cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
 cudaError_t launch_pair_grads(const PairGradParams &P, int G, cudaStream_t st);
 cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);

@@ -22,10 +22,10 @@
 
 namespace raygs {
 
-template <int TW, int TH, int PX, bool COUNT>
+template <int TW, int TH, int PX, int NBF, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P) {
   constexpr int NT = TW * TH / PX;  // threads
-  constexpr int NB = NT;            // records per batch
+  constexpr int NB = NBF * NT;      // records per batch
   constexpr int QX = TW / PX;       // threads per tile row
   __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
   __shared__ Rec s_raw[NB];
@@ -160,20 +160,24 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
   }
 }
 
-cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
-                          cudaStream_t st) {
+cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
+                          bool count, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   const unsigned grid = unsigned(n_tiles);
-#define RAYGS_RENDER_CASE(TW, TH, PX)                                                  \
-  if (tile_w == TW && tile_h == TH) {                                                  \
-    if (count) render_kernel<TW, TH, PX, true><<<grid, TW * TH / PX, 0, st>>>(P);      \
-    else render_kernel<TW, TH, PX, false><<<grid, TW * TH / PX, 0, st>>>(P);           \
-    return cudaGetLastError();                                                         \
+#define RAYGS_RENDER_CASE(TW, TH, PX, NBF)                                                      \
+  if (tile_w == TW && tile_h == TH && batch_records == NBF) {                                  \
+    if (count) render_kernel<TW, TH, PX, NBF, true><<<grid, TW * TH / PX, 0, st>>>(P);         \
+    else render_kernel<TW, TH, PX, NBF, false><<<grid, TW * TH / PX, 0, st>>>(P);              \
+    return cudaGetLastError();                                                                 \
   }
-  RAYGS_RENDER_CASE(16, 16, 4)
-  RAYGS_RENDER_CASE(16, 8, 4)
-  RAYGS_RENDER_CASE(32, 16, 8)
-  RAYGS_RENDER_CASE(8, 8, 2)
+  RAYGS_RENDER_CASE(16, 16, 4, 1)
+  RAYGS_RENDER_CASE(16, 8, 4, 1)
+  RAYGS_RENDER_CASE(32, 16, 8, 1)
+  RAYGS_RENDER_CASE(8, 8, 2, 1)
+  RAYGS_RENDER_CASE(16, 16, 4, 2)
+  RAYGS_RENDER_CASE(16, 8, 4, 2)
+  RAYGS_RENDER_CASE(32, 16, 8, 2)
+  RAYGS_RENDER_CASE(8, 8, 2, 2)
 #undef RAYGS_RENDER_CASE
   return cudaErrorInvalidValue;
 }

@@ -34,7 +34,7 @@ class Config(C.Structure):
     _fields_ = [("p_min", C.c_float), ("t_stop", C.c_float), ("alpha_max", C.c_float),
                 ("mip_sigma2", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("fp64_degenerate", C.c_int32), ("degenerate_ratio", C.c_float),
-                ("enable_backward", C.c_int32)]
+                ("enable_backward", C.c_int32), ("batch_records", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -268,6 +268,8 @@ def raygs_graph_launch(plan, stream=None):
 
 
 TILE_CANDIDATES = [(16, 16), (16, 8), (32, 16), (8, 8)]
+# autotuner candidates in its order: (tile_w, tile_h, batch_records), shape-major
+AUTOTUNE_CANDIDATES = [(w, h, b) for (w, h) in TILE_CANDIDATES for b in (1, 2)]
 
 
 def raygs_autotune_workspace_bytes(cams, n_gaussians: int, max_instances: int, cfg: Config | None = None) -> int:
@@ -278,15 +280,16 @@ def raygs_autotune_workspace_bytes(cams, n_gaussians: int, max_instances: int, c
 
 def raygs_autotune(cams, scene: Scene, max_instances: int, cfg: Config, workspace, rgb, T_final=None,
                    n_contrib=None, iters: int = 3, stream=None):
-    """Pick the fastest tile shape (written into cfg); returns {shape: ms per pass}."""
+    """Pick the fastest tile shape and rasteriser batch (written into cfg); returns
+    {"WxH/bN": ms per pass}."""
     arr = cams if isinstance(cams, C.Array) else make_cameras(cams)
-    ms = (C.c_float * len(TILE_CANDIDATES))()
+    ms = (C.c_float * len(AUTOTUNE_CANDIDATES))()
     _check(lib().raygs_autotune(arr, len(arr), C.byref(scene), int(max_instances), C.byref(cfg),
                                 workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                 rgb.data_ptr(), T_final.data_ptr() if T_final is not None else None,
                                 n_contrib.data_ptr() if n_contrib is not None else None, int(iters),
                                 stream_ptr(stream), ms), "raygs_autotune")
-    return {f"{w}x{h}": float(ms[i]) for i, (w, h) in enumerate(TILE_CANDIDATES)}
+    return {f"{w}x{h}/b{b}": float(ms[i]) for i, (w, h, b) in enumerate(AUTOTUNE_CANDIDATES)}
 
 
 def autotune(cams, scene_t: dict, capacity: int, device="cuda", iters: int = 3, **cfg_kw):
@@ -302,7 +305,7 @@ def autotune(cams, scene_t: dict, capacity: int, device="cuda", iters: int = 3, 
     nc = torch.empty(npx, dtype=torch.int32, device=device)
     times = raygs_autotune(cams, make_scene(scene_t), capacity, cfg, ws, rgb, T, nc, iters)
     del ws
-    return dict(cfg_kw, tile_w=int(cfg.tile_w), tile_h=int(cfg.tile_h)), times
+    return dict(cfg_kw, tile_w=int(cfg.tile_w), tile_h=int(cfg.tile_h), batch_records=int(cfg.batch_records)), times
 
 
 def raygs_render_noalloc(cams, scene: Scene, cfg: Config | None, rgb, T_final=None, n_contrib=None,

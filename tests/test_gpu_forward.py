@@ -194,10 +194,10 @@ def test_autotuner_picks_a_compiled_shape(oracle_lib):
     cams = [scenes.make_camera(96, 72, 80.0, 80.0), scenes.make_camera(50, 41, 40.0, 40.0, R=R1, t=t1)]
     st = raygs.scene_to_device(scene)
     kw, times = raygs.autotune(cams, st, capacity=1 << 20)
-    assert (kw["tile_w"], kw["tile_h"]) in raygs.TILE_CANDIDATES
-    assert all(v > 0 for v in times.values()), times
-    assert times[f"{kw['tile_w']}x{kw['tile_h']}"] == min(times.values())
-    check_views(scene, cams, oracle_lib, tile_w=kw["tile_w"], tile_h=kw["tile_h"])
+    assert (kw["tile_w"], kw["tile_h"], kw["batch_records"]) in raygs.AUTOTUNE_CANDIDATES
+    assert len(times) == 8 and all(v > 0 for v in times.values()), times
+    assert times[f"{kw['tile_w']}x{kw['tile_h']}/b{kw['batch_records']}"] == min(times.values())
+    check_views(scene, cams, oracle_lib, tile_w=kw["tile_w"], tile_h=kw["tile_h"], batch_records=kw["batch_records"])
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (16, 8), (32, 16), (8, 8)])
