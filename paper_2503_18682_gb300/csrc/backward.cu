@@ -31,6 +31,28 @@ __device__ __forceinline__ uint32_t emission_index(const BackParams &P, uint32_t
   return P.seg_off[rs] + (tx - txa);
 }
 
+// Sum 16 per-lane values over the warp by recursive halving: at each step a lane keeps half
+// of its values and adds its partner's copy of them (16 shuffles in all, against 80 for 16
+// separate butterflies).  Afterwards lane L holds the warp total of component
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of L); lanes L and L ^ 1 hold the same one.
+__device__ __forceinline__ float warp_sum16(float v[16], int lane) {
+#pragma unroll
+  for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool upper = lane & o;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? v[i] : v[i + half];
+      const float keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int warp_sum16_component(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 template <int TW, int TH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams P) {
   constexpr int NT = TW * TH / PX;
@@ -151,21 +173,14 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
         }
       }
       if (__any_sync(0xffffffffu, any)) {
+        float v16[16];
 #pragma unroll
-        for (int c = 0; c < kGradW; ++c) {
-          float v = acc[c];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          acc[c] = v;
-        }
-        if (lane == 0) {
-          if (NW == 1) {
-#pragma unroll
-            for (int c = 0; c < kGradW; ++c) s_acc[j][c] += acc[c];
-          } else {
-#pragma unroll
-            for (int c = 0; c < kGradW; ++c) atomicAdd(&s_acc[j][c], acc[c]);
-          }
+        for (int c = 0; c < 16; ++c) v16[c] = c < kGradW ? acc[c] : 0.f;
+        const float tot = warp_sum16(v16, lane);
+        const int c = warp_sum16_component(lane);
+        if ((lane & 1) == 0 && c < kGradW) {
+          if (NW == 1) s_acc[j][c] += tot;
+          else atomicAdd(&s_acc[j][c], tot);
         }
       }
     }
@@ -210,19 +225,12 @@ __global__ void __launch_bounds__(256) pair_grads_kernel(PairGradParams P) {
 #pragma unroll
       for (int c = 0; c < kGradW; ++c) acc[c] += P.partials[size_t(e) * kGradW + c];
     }
+    float v16[16];
 #pragma unroll
-    for (int c = 0; c < kGradW; ++c) {
-      float v = acc[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[c] = v;
-    }
-    if (lane < kGradW) {
-      float v = acc[0];
-#pragma unroll
-      for (int c = 1; c < kGradW; ++c) v = lane == c ? acc[c] : v;
-      P.pg[size_t(P.pairs[p]) * kGradW + lane] = v;
-    }
+    for (int c = 0; c < 16; ++c) v16[c] = c < kGradW ? acc[c] : 0.f;
+    const float tot = warp_sum16(v16, lane);
+    const int c = warp_sum16_component(lane);
+    if ((lane & 1) == 0 && c < kGradW) P.pg[size_t(P.pairs[p]) * kGradW + c] = tot;
   }
 }
 
@@ -277,18 +285,16 @@ __device__ void view_whitening(const float muf[3], const df muc[3], const T Rp[9
   for (int i = 0; i < 9; ++i) Rc_out[i] = float(Rc[i]);
 }
 
+// Chain rule of one primitive over the views where it is visible; SH gradients are
+// accumulated into dsh, the other parameter gradients written directly.
 template <int DEG>
-__global__ void __launch_bounds__(128) param_grads_kernel(ParamGradParams P) {
+__device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g, const float *coef, float *dsh) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.n) return;
   const float mx = P.means[3 * int64_t(g)], my = P.means[3 * int64_t(g) + 1], mz = P.means[3 * int64_t(g) + 2];
   float ls[3], q4[4];
   for (int k = 0; k < 3; ++k) ls[k] = load_attr(P.log_scales, 3 * int64_t(g) + k, P.scale_dtype);
   for (int k = 0; k < 4; ++k) q4[k] = P.quats[4 * int64_t(g) + k];
   const float logit = load_attr(P.logits, g, P.opacity_dtype);
-  float coef[3 * K];
-  for (int k = 0; k < 3 * K; ++k) coef[k] = load_attr(P.sh, int64_t(g) * 3 * K + k, P.sh_dtype);
   float Rp[9];
   quat_rot<float>(q4[0], q4[1], q4[2], q4[3], Rp);
   const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
@@ -304,10 +310,9 @@ __global__ void __launch_bounds__(128) param_grads_kernel(ParamGradParams P) {
     for (int k = 0; k < 3; ++k) sd[k] = exp(double(ls[k]));
   }
 
-  float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dRp[9], dlogit = 0.f, dsh[3 * K];
+  float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dRp[9], dlogit = 0.f;
 #pragma unroll
   for (int i = 0; i < 9; ++i) dRp[i] = 0.f;
-  for (int i = 0; i < 3 * K; ++i) dsh[i] = 0.f;
 
   for (int v = 0; v < P.n_views; ++v) {
     const int64_t idx = int64_t(v) * P.n + g;
@@ -437,8 +442,32 @@ __global__ void __launch_bounds__(128) param_grads_kernel(ParamGradParams P) {
     P.d_quats[4 * int64_t(g) + 3] = (gz - z * dot) * qn;
   }
   if (P.d_logits) P.d_logits[g] = dlogit;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) param_grads_kernel(ParamGradParams P) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int K3 = 3 * K, SHP = K3 + 1;  // padded row
+  // SH coefficients in and their gradients out go through shared memory with coalesced
+  // 16-byte transfers (one row of 3K values per primitive)
+  __shared__ float s_sh[128 * SHP];
+  const int g0 = blockIdx.x * blockDim.x;
+  const int nb = min(int(blockDim.x), P.n - g0);
+  stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, 1);
+  __syncthreads();
+  const int g = g0 + threadIdx.x;
+  const bool active = g < P.n;
+  const float *coef = s_sh + threadIdx.x * SHP;
+  float dsh[3 * K];
+  for (int i = 0; i < 3 * K; ++i) dsh[i] = 0.f;
+  if (active) param_grads_one<DEG>(P, g, coef, dsh);
+  __syncthreads();
   if (P.d_sh) {
-    for (int k = 0; k < 3 * K; ++k) P.d_sh[int64_t(g) * 3 * K + k] = dsh[k];
+    if (active)
+      for (int k = 0; k < K3; ++k) s_sh[threadIdx.x * SHP + k] = dsh[k];
+    __syncthreads();
+    float *dst = P.d_sh + int64_t(g0) * K3;
+    for (int e = threadIdx.x; e < nb * K3; e += blockDim.x) dst[e] = s_sh[(e / K3) * SHP + e % K3];
   }
 }
 

@@ -228,43 +228,6 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
   return true;
 }
 
-// Cooperative copy of `count` consecutive attributes starting at element `first` of `src`
-// into float32 shared memory, 16-byte vector loads where aligned.  dst element e goes to
-// dst[(e / row) * (row + pad) + e % row] (pad breaks shared-memory bank conflicts).
-__device__ void stage_attr(float *dst, const void *src, int64_t first, int count, int dtype,
-                           int row, int pad) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  auto put = [&](int e, float v) { dst[(e / row) * (row + pad) + e % row] = v; };
-  if (dtype == RAYGS_F32) {
-    const float *s = reinterpret_cast<const float *>(src) + first;
-    int nvec = ((reinterpret_cast<uintptr_t>(s) & 15) == 0) ? count / 4 : 0;
-    const float4 *s4 = reinterpret_cast<const float4 *>(s);
-    for (int i = tid; i < nvec; i += nt) {
-      float4 v = __ldg(s4 + i);
-      put(4 * i, v.x); put(4 * i + 1, v.y); put(4 * i + 2, v.z); put(4 * i + 3, v.w);
-    }
-    for (int e = 4 * nvec + tid; e < count; e += nt) put(e, __ldg(s + e));
-  } else {
-    const uint16_t *s = reinterpret_cast<const uint16_t *>(src) + first;
-    int nvec = ((reinterpret_cast<uintptr_t>(s) & 15) == 0) ? count / 8 : 0;
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(s);
-    auto cvt = [&](uint16_t b) -> float {
-      if (dtype == RAYGS_F16) return __half2float(__ushort_as_half(b));
-      return __uint_as_float(uint32_t(b) << 16);
-    };
-    for (int i = tid; i < nvec; i += nt) {
-      uint4 v = __ldg(s4 + i);
-      uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        put(8 * i + 2 * j, cvt(uint16_t(w[j] & 0xFFFF)));
-        put(8 * i + 2 * j + 1, cvt(uint16_t(w[j] >> 16)));
-      }
-    }
-    for (int e = 8 * nvec + tid; e < count; e += nt) put(e, cvt(__ldg(s + e)));
-  }
-}
-
 __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, const DevCam &cam,
                                              const df muc[3], const StageOut &so, const float rgb[3],
                                              float z) {
