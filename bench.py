@@ -378,10 +378,10 @@ def run_ours(args, world, rank, local):
     prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
     # kernels per pass: preprocess (2), depth sort (4 passes x 5), row-count scan (3),
     # row spans (1), tile-row instance scan (1), tile-row sort (passes x 5), tile-row
-    # ranges (1), instance lists (1), rasteriser (1)
+    # ranges (1), chunk scan + chunk counts + instance lists (3), rasteriser (1)
     trows = sum(-(-c["height"] // r.cfg.tile_h) for c in cams)
     row_passes = (max(1, (trows - 1).bit_length()) + 7) // 8
-    gpu_launches = args.steps * (2 + 20 + 3 + 1 + 1 + 5 * row_passes + 1 + 1 + 1)
+    gpu_launches = args.steps * (2 + 20 + 3 + 1 + 1 + 5 * row_passes + 1 + 3 + 1)
 
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,

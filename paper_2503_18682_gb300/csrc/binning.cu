@@ -747,15 +747,94 @@ cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters 
 // lanes that cover the same tile.  Each tile's list keeps depth order.  The masks are
 // double-buffered (the buffer of the next step is cleared while this one is read) and the
 // rows of the next step are loaded during this one.
+// The chunk of rows a CTA owns: tile row t (largest t with chunk_base[t] <= chunk) and its
+// rows [first, last).
+__device__ __forceinline__ bool chunk_of(const ExpandParams &E, uint32_t chunk, int &t, int &c, uint2 &rows) {
+  if (chunk >= E.chunk_base[E.trows]) return false;
+  int lo = 0, hi = E.trows - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (E.chunk_base[m] <= chunk) lo = m; else hi = m - 1;
+  }
+  t = lo;
+  c = int(chunk - E.chunk_base[t]);
+  const uint2 rr = E.trow_ranges[t];
+  const uint32_t first = rr.x + uint32_t(c) * uint32_t(E.chunk_rows);
+  rows = make_uint2(min(first, rr.y), min(first + uint32_t(E.chunk_rows), rr.y));
+  return true;
+}
+
+// Chunks per tile row (at least one) and their exclusive scan (one block).
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(ExpandParams E) {
+  __shared__ uint32_t ws[33];
+  const int per = (E.trows + 1023) / 1024;
+  const int b = min(E.trows, int(threadIdx.x) * per), e = min(E.trows, b + per);
+  auto nchunks = [&](int t) {
+    const uint2 rr = E.trow_ranges[t];
+    const uint32_t n = rr.y - rr.x;
+    return n == 0 ? 1u : (n + uint32_t(E.chunk_rows) - 1) / uint32_t(E.chunk_rows);
+  };
+  uint32_t s = 0;
+  for (int t = b; t < e; ++t) s += nchunks(t);
+  uint32_t tot;
+  uint32_t run = block_excl_scan(s, ws, &tot);
+  for (int t = b; t < e; ++t) {
+    E.chunk_base[t] = run;
+    run += nchunks(t);
+  }
+  if (threadIdx.x == 0) E.chunk_base[E.trows] = min(tot, uint32_t(E.max_chunks));
+}
+
+// Instances per tile column of one chunk: each row covers the tile columns
+// [txa, txa + len); a difference array over the columns and its prefix sum count them.
+__global__ void __launch_bounds__(256) chunk_count_kernel(ExpandParams E) {
+  extern __shared__ uint32_t s_diff[];  // [max_tiles_x + 1]
+  __shared__ uint32_t s_ws[33];
+  int t, c;
+  uint2 rows;
+  if (!chunk_of(E, blockIdx.x, t, c, rows)) return;
+  int v;
+  const DevCam &cam = view_of_trow(E, t, v);
+  const int TX = cam.tiles_x;
+  for (int x = threadIdx.x; x <= TX; x += blockDim.x) s_diff[x] = 0u;
+  __syncthreads();
+  for (uint32_t i = rows.x + threadIdx.x; i < rows.y; i += blockDim.x) {
+    const uint32_t pk = E.rows[i].y;
+    atomicAdd(&s_diff[pk & 0xFFFFu], 1u);
+    atomicSub(&s_diff[(pk & 0xFFFFu) + (pk >> 16)], 1u);
+  }
+  __syncthreads();
+  const int per = (TX + int(blockDim.x) - 1) / int(blockDim.x);
+  const int x0 = min(TX, int(threadIdx.x) * per), x1 = min(TX, x0 + per);
+  uint32_t dsum = 0;
+  for (int x = x0; x < x1; ++x) dsum += s_diff[x];
+  uint32_t dtot;
+  uint32_t run = block_excl_scan(dsum, s_ws, &dtot);
+  uint32_t *out = E.chunk_cnt + size_t(blockIdx.x) * size_t(E.max_tiles_x);
+  for (int x = x0; x < x1; ++x) {
+    run += s_diff[x];
+    out[x] = run;
+  }
+}
+
+// Instance lists of one chunk of a tile row.  Its cursor in tile column x starts after the
+// tile row's earlier tiles (all chunks) and after the earlier chunks' instances in x; chunk 0
+// also writes the tile row's ranges.  Rows are then taken in sorted (depth) order, NT * KR
+// at a time, in 32-row groups (KR * NT / 32 groups: row q of the step is lane q % 32 of group
+// q / 32); every lane marks the tiles of its row in its group's bit mask per tile, and the
+// rank of (row, tile) is the tile's running cursor plus the rows of lower groups and lower
+// lanes that cover the same tile.  Each tile's list keeps depth order.  The masks are
+// double-buffered (the buffer of the next step is cleared while this one is read) and the
+// rows of the next step are loaded during this one.
 template <int NT, int KR>
 __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
   constexpr int VW = NT / 32 * KR;  // row groups per step
   extern __shared__ uint32_t s_mem[];
-  __shared__ int s_v;
-  const int grow = blockIdx.x;
-  if (threadIdx.x == 0) { int v; view_of_trow(E, grow, v); s_v = v; }
-  __syncthreads();
-  const DevCam &cam = E.cams[s_v];
+  int grow, chunk_c;
+  uint2 rr;
+  if (!chunk_of(E, blockIdx.x, grow, chunk_c, rr)) return;
+  int v;
+  const DevCam &cam = view_of_trow(E, grow, v);
   const int TX = cam.tiles_x;
   const int TP = TX | 1;                     // odd row stride: no bank conflicts down a column
   uint32_t *s_cur = s_mem;                   // [TX] next free slot of each tile
@@ -764,41 +843,35 @@ __global__ void __launch_bounds__(NT) expand_kernel(ExpandParams E) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t tile0 = uint32_t(cam.tile_base) + uint32_t(grow - cam.trow_base) * uint32_t(TX);
-  // Instances per tile of this tile row: each row covers the tile columns [txa, txa + len);
-  // a difference array over the columns (in the group-prefix buffer) and its prefix sum
-  // count them, and their exclusive scan from the tile row's first instance places them.
-  const uint2 rr = E.trow_ranges[grow];
-  uint32_t *s_diff = s_pre;  // TX + 1 words (VW * TP >= TX + 1)
-  for (int x = threadIdx.x; x <= TX; x += NT) s_diff[x] = 0u;
-  __syncthreads();
-  for (uint32_t i = rr.x + threadIdx.x; i < rr.y; i += NT) {
-    const uint32_t pk = E.rows[i].y;
-    const uint32_t xa = pk & 0xFFFFu, len = pk >> 16;
-    atomicAdd(&s_diff[xa], 1u);
-    atomicSub(&s_diff[xa + len], 1u);
-  }
-  __syncthreads();
   {
+    // per tile column: instances of the whole tile row and of the earlier chunks
+    const uint32_t cb = E.chunk_base[grow], nch = E.chunk_base[grow + 1] - cb;
+    uint32_t *s_tot = s_pre, *s_bef = s_pre + TX;  // 2 TX words of the group-prefix buffer
+    for (int x = threadIdx.x; x < TX; x += NT) {
+      uint32_t tot = 0, bef = 0;
+      for (uint32_t k = 0; k < nch; ++k) {
+        const uint32_t n = E.chunk_cnt[size_t(cb + k) * size_t(E.max_tiles_x) + x];
+        tot += n;
+        bef += k < uint32_t(chunk_c) ? n : 0u;
+      }
+      s_tot[x] = tot;
+      s_bef[x] = bef;
+    }
+    __syncthreads();
     __shared__ uint32_t s_ws[33];
     const int per = (TX + NT - 1) / NT;
     const int x0 = min(TX, int(threadIdx.x) * per), x1 = min(TX, x0 + per);
-    uint32_t dsum = 0;
-    for (int x = x0; x < x1; ++x) dsum += s_diff[x];
-    uint32_t dtot;
-    const uint32_t dpre = block_excl_scan(dsum, s_ws, &dtot);  // differences before the chunk
-    uint32_t csum = 0, run = dpre;
-    for (int x = x0; x < x1; ++x) { run += s_diff[x]; csum += run; }
-    __syncthreads();
+    uint32_t csum = 0;
+    for (int x = x0; x < x1; ++x) csum += s_tot[x];
     uint32_t ctot;
-    const uint32_t cpre = block_excl_scan(csum, s_ws, &ctot);  // instances before the chunk
+    const uint32_t cpre = block_excl_scan(csum, s_ws, &ctot);  // instances before the column chunk
     const unsigned long long base = E.trow_base[grow];
     uint32_t o = uint32_t(min(base, (unsigned long long)E.cap)) + cpre;
-    run = dpre;
     for (int x = x0; x < x1; ++x) {
-      run += s_diff[x];  // this tile's instance count
-      s_cur[x] = o;
-      E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + run, E.cap));
-      o += run;
+      const uint32_t n = s_tot[x];
+      s_cur[x] = o + s_bef[x];
+      if (chunk_c == 0) E.ranges[tile0 + x] = make_uint2(min(o, E.cap), min(o + n, E.cap));
+      o += n;
     }
   }
   __syncthreads();
@@ -861,20 +934,35 @@ size_t expand_smem(int max_tiles_x) {
 }
 
 
-cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st) {
-  if (n_trows == 0) return cudaSuccess;
+int expand_chunk_rows(int64_t cap, int max_tiles_x) {
+  // 8192 rows per chunk, more when the per-chunk column counts would pass 32 M entries
+  int64_t ch = 8192;
+  const int64_t need = (cap * int64_t(max_tiles_x > 0 ? max_tiles_x : 1)) / (int64_t(32) << 20) + 1;
+  if (need > ch) ch = need;
+  return int(ch > (int64_t(1) << 30) ? (int64_t(1) << 30) : ch);
+}
+
+int64_t expand_max_chunks(int64_t trows, int64_t cap, int chunk_rows) {
+  return trows + cap / chunk_rows + 1;
+}
+
+cudaError_t launch_expand(const ExpandParams &E, cudaStream_t st) {
+  if (E.trows == 0) return cudaSuccess;
+  chunk_scan_kernel<<<1, 1024, 0, st>>>(E);
+  chunk_count_kernel<<<E.max_chunks, 256, sizeof(uint32_t) * size_t(E.max_tiles_x + 1), st>>>(E);
   constexpr size_t kBudget = 200 * 1024;
   auto run = [&](auto kernel, int nt, size_t smem) -> cudaError_t {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
     }
-    kernel<<<n_trows, nt, smem, st>>>(E);
+    kernel<<<E.max_chunks, nt, smem, st>>>(E);
     return cudaGetLastError();
   };
-  if (expand_smem<256, 4>(max_tiles_x) <= kBudget) return run(expand_kernel<256, 4>, 256, expand_smem<256, 4>(max_tiles_x));
-  if (expand_smem<256, 1>(max_tiles_x) <= kBudget) return run(expand_kernel<256, 1>, 256, expand_smem<256, 1>(max_tiles_x));
-  return run(expand_kernel<128, 1>, 128, expand_smem<128, 1>(max_tiles_x));
+  const int mtx = E.max_tiles_x;
+  if (expand_smem<256, 4>(mtx) <= kBudget) return run(expand_kernel<256, 4>, 256, expand_smem<256, 4>(mtx));
+  if (expand_smem<256, 1>(mtx) <= kBudget) return run(expand_kernel<256, 1>, 256, expand_smem<256, 1>(mtx));
+  return run(expand_kernel<128, 1>, 128, expand_smem<128, 1>(mtx));
 }
 
 }  // namespace raygs

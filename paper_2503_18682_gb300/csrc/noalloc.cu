@@ -87,13 +87,13 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  const Layout L0 = make_layout(n_views, n, tiles, trows, 0, w.G, false);
+  const Layout L0 = make_layout(n_views, n, tiles, trows, 0, w.G, max_tx, false);
   if (L0.total + 8192 > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   int64_t cap = int64_t((kNoAllocScratchBytes - L0.total - 8192) / (kBytesPerCapacity + 1));
-  w.L = make_layout(n_views, n, tiles, trows, cap, w.G, false);
+  w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false);
   while (w.L.total > kNoAllocScratchBytes && cap > 0) {
     cap -= 4096;
-    w.L = make_layout(n_views, n, tiles, trows, cap, w.G, false);
+    w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false);
   }
   if (cap <= 0 || w.L.total > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   w.cap = cap;

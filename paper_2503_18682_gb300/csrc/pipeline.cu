@@ -73,7 +73,8 @@ int tile_sort_bits(int64_t tiles) {
   return b;
 }
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, bool backward) {
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, int max_tiles_x,
+                   bool backward) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = up256(o + bytes); return r; };
@@ -100,6 +101,10 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.inst = take(4 * C + 16);
   L.trange = take(8 * size_t(trows) + 16);
   L.trinst = take(8 * size_t(trows) + 16);
+  const int chunk_rows = expand_chunk_rows(cap, max_tiles_x);
+  const int64_t max_chunks = expand_max_chunks(trows, cap, chunk_rows);
+  L.cbase = take(4 * size_t(trows + 1) + 16);
+  L.ccnt = take(4 * size_t(max_chunks) * size_t(max_tiles_x > 0 ? max_tiles_x : 1) + 16);
   L.hist = take(4 * 512 * size_t(G) + 4 * (512 * size_t(G) / 2048 + 1));
   L.ranges = take(8 * size_t(tiles));
   L.deg = take(4 * VN);
@@ -282,7 +287,13 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   X.ranges = w.at<uint2>(w.L.ranges);
   X.inst = w.at<uint32_t>(w.L.inst);
   X.cap = cap;
-  return launch_expand(X, int(w.trows), w.max_tiles_x, st);
+  X.chunk_base = w.at<uint32_t>(w.L.cbase);
+  X.chunk_cnt = w.at<uint32_t>(w.L.ccnt);
+  X.chunk_rows = expand_chunk_rows(w.cap, w.max_tiles_x);
+  X.trows = int(w.trows);
+  X.max_tiles_x = w.max_tiles_x;
+  X.max_chunks = int(expand_max_chunks(w.trows, w.cap, X.chunk_rows));
+  return launch_expand(X, st);
 }
 
 cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_contrib, bool count,

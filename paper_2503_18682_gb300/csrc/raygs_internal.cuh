@@ -235,6 +235,12 @@ struct ExpandParams {
   uint2 *ranges;             // [tiles] instance range of every tile (clamped to cap)
   uint32_t *inst;            // [cap] sorted pair position of every instance
   uint32_t cap;
+  // Each tile row's sorted rows are cut into chunks of chunk_rows rows (at least one chunk
+  // per tile row), one CTA each: chunk_base[t] is tile row t's first chunk (chunk_base[trows]
+  // the number of chunks), chunk_cnt[chunk][x] the chunk's instances in tile column x.
+  uint32_t *chunk_base;
+  uint32_t *chunk_cnt;
+  int chunk_rows, trows, max_tiles_x, max_chunks;
 };
 
 struct RenderParams {
@@ -308,7 +314,9 @@ cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
 cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st);
-cudaError_t launch_expand(const ExpandParams &E, int n_trows, int max_tiles_x, cudaStream_t st);
+cudaError_t launch_expand(const ExpandParams &E, cudaStream_t st);
+int expand_chunk_rows(int64_t cap, int max_tiles_x);
+int64_t expand_max_chunks(int64_t trows, int64_t cap, int chunk_rows);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
                           bool count, cudaStream_t st);
 cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
@@ -319,11 +327,12 @@ cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
   size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], off, partial, rtstart,
-      seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, inst, hist, ranges, deg, degc, partials, pg, total;
+      seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, cbase, ccnt, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };
 
-Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, bool backward);
+Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, int max_tiles_x,
+                   bool backward);
 
 // Workspace bytes per unit of instance capacity (tile rows and instances share it).
 constexpr size_t kBytesPerCapacity = 8 + 4 + 4 + 2 * 4 + 2 * 8 + 4;
