@@ -549,6 +549,7 @@ __device__ bool support_tile_span(const Rec &r, const DevCam &cam, int tile_w, f
 __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   __shared__ uint32_t s_off[kEmitTile + 1];
   __shared__ uint32_t s_pair[kEmitTile + 1];
+  __shared__ uint16_t s_owner[kEmitTile];     // the tile's pair (local index) of each row
   __shared__ uint32_t s_trow[kTrowsShared];  // this CTA's instances per tile row
   const bool shared_trows = R.trows <= kTrowsShared;
   if (shared_trows)
@@ -568,8 +569,13 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
       s_pair[j] = R.pairs[p_lo + j];
     }
     __syncthreads();
-    // two rows per thread at a time: both pair look-ups and their loads are issued before
-    // either row's arithmetic
+    // each pair marks its rows in this tile with its local index
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+      const uint32_t first = max(s_off[j], e0), next = j + 1 < np ? min(s_off[j + 1], e1) : e1;
+      for (uint32_t e = first; e < next; ++e) s_owner[e - e0] = uint16_t(j);
+    }
+    __syncthreads();
+    // two rows per thread at a time: both loads are issued before either row's arithmetic
     for (uint32_t e_base = e0; e_base < e1; e_base += 2 * blockDim.x) {
       uint32_t ee[2];
       int aa[2];
@@ -577,12 +583,7 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         ee[u] = e_base + u * blockDim.x + threadIdx.x;
-        int a = 0, b = np - 1;
-        const uint32_t e = min(ee[u], e1 - 1);
-        while (a < b) {
-          int m = (a + b + 1) >> 1;
-          if (s_off[m] <= e) a = m; else b = m - 1;
-        }
+        const int a = s_owner[min(ee[u], e1 - 1) - e0];
         aa[u] = a;
         const uint32_t pair = s_pair[a];
         el2[u] = R.ell[pair];
