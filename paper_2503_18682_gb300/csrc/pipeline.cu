@@ -26,6 +26,8 @@ void fill_devcam(const raygs_camera &c, const raygs_config &cfg, DevCam &d) {
   d.xmax = float((double(c.width) - 0.5 - double(c.cx)) / double(c.fx));
   d.ymin = float((0.5 - double(c.cy)) / double(c.fy));
   d.ymax = float((double(c.height) - 0.5 - double(c.cy)) / double(c.fy));
+  const float sl[4] = {d.xmin, d.xmax, d.ymin, d.ymax};
+  for (int k = 0; k < 4; ++k) d.fn[k] = float(std::sqrt(1.0 + double(sl[k]) * double(sl[k])));
   d.tiles_x = (c.width + cfg.tile_w - 1) / cfg.tile_w;
   d.tiles_y = (c.height + cfg.tile_h - 1) / cfg.tile_h;
 }

@@ -32,10 +32,8 @@ struct StageOut {
 // the view's frustum (through the outermost pixel-centre rays).
 template <typename T>
 __device__ __forceinline__ bool outside_frustum(const T mu[3], T rad, const DevCam &cam) {
-  return mu[0] - T(cam.xmin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.xmin) * T(cam.xmin)) ||
-         T(cam.xmax) * mu[2] - mu[0] < -rad * t_sqrt(T(1) + T(cam.xmax) * T(cam.xmax)) ||
-         mu[1] - T(cam.ymin) * mu[2] < -rad * t_sqrt(T(1) + T(cam.ymin) * T(cam.ymin)) ||
-         T(cam.ymax) * mu[2] - mu[1] < -rad * t_sqrt(T(1) + T(cam.ymax) * T(cam.ymax));
+  return mu[0] - T(cam.xmin) * mu[2] < -rad * T(cam.fn[0]) || T(cam.xmax) * mu[2] - mu[0] < -rad * T(cam.fn[1]) ||
+         mu[1] - T(cam.ymin) * mu[2] < -rad * T(cam.fn[2]) || T(cam.ymax) * mu[2] - mu[1] < -rad * T(cam.fn[3]);
 }
 
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame

@@ -24,6 +24,7 @@ struct DevCam {
   int mip;
   float C[3];                  // camera centre in the world frame
   float xmin, xmax, ymin, ymax;  // slopes of the outermost pixel-centre rays
+  float fn[4];                 // sqrt(1 + slope^2) of each: norms of the side-plane normals
   int tiles_x, tiles_y;
   int tile_base;               // first global tile id of the view
   int trow_base;               // first global tile row of the view
