@@ -412,11 +412,63 @@ def run_ours(args, world, rank, local):
     )
     if not args.no_backward:
         line["fwd_bwd"] = fwd_bwd_ms_per_view(args, dev)
+    if not args.no_precision:
+        line["precision_storage"] = precision_storage(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def precision_storage(args, dev):
+    """The 6M-primitive precision workload (4 views at 3840x2160 plus the same poses at
+    960x540 with the MIP filter) with SH and log-scales stored in FP16 or BF16 and opacity
+    logits in FP16, against the FP32 form on the same GPU: forward time of each form and
+    the image error of the reduced forms (max-abs over the RGB channels, PSNR for a unit
+    range).  All arithmetic is FP32 in every form."""
+    import torch
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene, cams = scenes.workload_precision()
+    n = int(scene["means"].shape[0])
+    out, ref = {}, None
+    for form in ("f32", "f16", "bf16"):
+        sc_np = scene if form == "f32" else scenes.to_storage(scene, form)
+        st = raygs.scene_to_device(sc_np, dev)
+        attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
+        r = raygs.Renderer(cams, n, device=dev)
+        rgb, T, nc = r.forward(st)
+        r.capacity = int(r.last_counters["n_instances"] * 1.05 + 65536)
+        r._make_plan()
+        rgb, T, nc = r.forward(st)
+        sc = raygs.make_scene(st)
+
+        def fwd():
+            raygs.raygs_preprocess(r.plan, sc)
+            raygs.raygs_bin_sort(r.plan)
+            raygs.raygs_render(r.plan, rgb, T, nc)
+
+        for _ in range(2):
+            fwd()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fwd()
+        e1.record()
+        e1.synchronize()
+        entry = dict(forward_ms=e0.elapsed_time(e1) / 3, attribute_bytes=int(attr_bytes))
+        if ref is None:
+            ref = rgb.clone()
+        else:
+            d = (rgb - ref).abs()
+            mse = float(((rgb - ref).double() ** 2).mean())
+            entry.update(max_abs_vs_f32=float(d.max()), psnr_vs_f32_db=(99.0 if mse == 0 else -10 * np.log10(mse)),
+                         frac_pixels_over_1e3=float((d.max(dim=1).values > 1e-3).double().mean()))
+        out[form] = entry
+        del r, st, rgb, T, nc
+        torch.cuda.empty_cache()
+    out["workload"] = f"{n} blob primitives, 4 views 3840x2160 + the same 4 poses at 960x540 with MIP"
+    return out
 
 
 def fwd_bwd_ms_per_view(args, dev):
@@ -487,6 +539,8 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP16/BF16 storage measurement on the 6M-primitive 4K workload")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="profile mode: tile shape WxH (default 16x16)")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
