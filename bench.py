@@ -414,11 +414,67 @@ def run_ours(args, world, rank, local):
         line["fwd_bwd"] = fwd_bwd_ms_per_view(args, dev)
     if not args.no_precision:
         line["precision_storage"] = precision_storage(args, dev)
+        line["antialiasing"] = antialiasing(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def antialiasing(args, dev):
+    """The 720p MIP workload (500k primitives, 1280x720) three ways: one ray per pixel
+    without the MIP term, with the paper's MIP term (Eq. mip), and 2x2 supersampled without
+    it (four sub-pixel rays, box-filter resolve; the counterpart of the paper's MSAA
+    comparison).  Forward time of each, and the first two images against the supersampled
+    one (max-abs, PSNR)."""
+    import torch
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene, cams_mip = scenes.workload_mip_720p()
+    n = int(scene["means"].shape[0])
+    st = raygs.scene_to_device(scene, dev)
+    sc = raygs.make_scene(st)
+    plain = [dict(c, mip=False) for c in cams_mip]
+
+    def timed_forward(cams):
+        r = raygs.Renderer(cams, n, device=dev)
+        rgb, T, nc = r.forward(st)
+        r.capacity = int(r.last_counters["n_instances"] * 1.05 + 65536)
+        r._make_plan()
+        rgb, T, nc = r.forward(st)
+
+        def fwd():
+            raygs.raygs_preprocess(r.plan, sc)
+            raygs.raygs_bin_sort(r.plan)
+            raygs.raygs_render(r.plan, rgb, T, nc)
+
+        for _ in range(2):
+            fwd()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            fwd()
+        e1.record()
+        e1.synchronize()
+        return r, rgb, e0.elapsed_time(e1) / 5
+
+    _, img_plain, ms_plain = timed_forward(plain)
+    _, img_mip, ms_mip = timed_forward(cams_mip)
+    r_ss, img_hi, ms_ss = timed_forward(raygs.supersampled_cameras(plain, 2))
+    img_ss = torch.empty_like(img_plain)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    raygs.raygs_resolve_supersampled(r_ss.plan, 2, img_hi, None, img_ss)
+    e1.record()
+    e1.synchronize()
+
+    def err(a):
+        mse = float(((a - img_ss).double() ** 2).mean())
+        return dict(max_abs=float((a - img_ss).abs().max()), psnr_db=(99.0 if mse == 0 else -10 * np.log10(mse)))
+
+    return dict(workload=f"{n} blob primitives, 1280x720", one_ray_ms=ms_plain, mip_ms=ms_mip,
+                supersampled_2x2_ms=ms_ss + e0.elapsed_time(e1),
+                one_ray_vs_supersampled=err(img_plain), mip_vs_supersampled=err(img_mip))
 
 
 def precision_storage(args, dev):

@@ -192,6 +192,19 @@ raygs_status raygs_render(raygs_plan *plan, float *rgb, float *T_final, int32_t 
                           void *stream);
 
 /*
+ * Supersampled anti-aliasing (a box-filter counterpart of the paper's MSAA comparison,
+ * Sec. 6; not part of its method): the plan's views were rendered at `factor` times the
+ * resolution (each camera's width, height, fx, fy, cx and cy multiplied by factor, so that a
+ * pixel's factor x factor block holds its sub-pixel rays).  Writes, per view in plan order,
+ * the mean of every block: rgb_lo [sum of (W/factor)(H/factor)][3] and, when both T
+ * pointers are non-NULL, T_lo likewise.  All buffers are caller-owned device memory.
+ * RAYGS_ERR_INVALID_ARG when a view's width or height is not a multiple of factor or
+ * factor is outside 1..16.
+ */
+raygs_status raygs_resolve_supersampled(const raygs_plan *plan, int32_t factor, const float *rgb_hi,
+                                        const float *T_hi, float *rgb_lo, float *T_lo, void *stream);
+
+/*
  * Gradients of a scalar loss L through raygs_render back to the scene parameters
  * (not in the paper, whose renderer is not differentiable; reverse mode of Eq. rendering,
  * Eq. rend_opacity and Eq. Q_ray).  Uses the workspace of the preceding forward pass (same

@@ -149,6 +149,25 @@ raygs_status raygs_plan_set_poses(raygs_plan *plan, const raygs_camera *cams, vo
 
 int64_t raygs_plan_num_pixels(const raygs_plan *plan) { return plan ? plan->total_pixels : 0; }
 int64_t raygs_plan_num_tiles(const raygs_plan *plan) { return plan ? plan->w.tiles : 0; }
+raygs_status raygs_resolve_supersampled(const raygs_plan *plan, int32_t factor, const float *rgb_hi,
+                                        const float *T_hi, float *rgb_lo, float *T_lo, void *stream) {
+  if (!plan || !rgb_hi || !rgb_lo || factor < 1 || factor > 16) return RAYGS_ERR_INVALID_ARG;
+  long long base_lo = 0;
+  for (int v = 0; v < plan->w.n_views; ++v) {
+    const raygs_camera &c = plan->cams[v];
+    if (c.width % factor != 0 || c.height % factor != 0) return RAYGS_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int v = 0; v < plan->w.n_views; ++v) {
+    const raygs_camera &c = plan->cams[v];
+    const int w_lo = c.width / factor, h_lo = c.height / factor;
+    cudaError_t e = launch_resolve(rgb_hi, T_hi, rgb_lo, T_lo, w_lo, h_lo, factor, plan->dcams[v].pix_base, base_lo, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    base_lo += (long long)w_lo * h_lo;
+  }
+  return RAYGS_OK;
+}
+
 int64_t raygs_plan_pixel_offset(const raygs_plan *plan, int32_t view) {
   if (!plan || view < 0 || view >= plan->w.n_views) return -1;
   return plan->dcams[view].pix_base;

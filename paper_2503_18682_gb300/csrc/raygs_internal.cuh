@@ -323,6 +323,8 @@ cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int bat
 cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
 cudaError_t launch_pair_grads(const PairGradParams &P, int G, cudaStream_t st);
 cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
+cudaError_t launch_resolve(const float *rgb_hi, const float *T_hi, float *rgb_lo, float *T_lo, int w_lo, int h_lo,
+                           int factor, long long base_hi, long long base_lo, cudaStream_t st);
 
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.

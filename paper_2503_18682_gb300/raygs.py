@@ -74,6 +74,8 @@ _SIGS = [
     ("raygs_preprocess", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p]),
     ("raygs_bin_sort", C.c_int, [C.c_void_p, C.c_void_p]),
     ("raygs_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("raygs_resolve_supersampled", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p]),
     ("raygs_render_backward", C.c_int, [C.c_void_p, C.POINTER(Scene), C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.POINTER(Grads), C.c_void_p]),
     ("raygs_read_counters", C.c_int, [C.c_void_p, C.POINTER(Counters), C.c_void_p]),
@@ -247,6 +249,29 @@ def raygs_render_backward(plan, scene: Scene, T_final, n_contrib, dL_drgb, dL_dT
     _check(lib().raygs_render_backward(plan, C.byref(scene), T_final.data_ptr(), n_contrib.data_ptr(),
                                        dL_drgb.data_ptr(), dL_dT.data_ptr() if dL_dT is not None else None,
                                        C.byref(grads), stream_ptr(stream)), "raygs_render_backward")
+
+
+def raygs_resolve_supersampled(plan, factor: int, rgb_hi, T_hi, rgb_lo, T_lo=None, stream=None):
+    """Box-filter resolve of views rendered at `factor` times the resolution (see
+    supersampled_cameras) into rgb_lo / T_lo."""
+    _check(lib().raygs_resolve_supersampled(plan, int(factor), rgb_hi.data_ptr(),
+                                            T_hi.data_ptr() if T_hi is not None else None, rgb_lo.data_ptr(),
+                                            T_lo.data_ptr() if T_lo is not None else None, stream_ptr(stream)),
+           "raygs_resolve_supersampled")
+
+
+def supersampled_cameras(cams, factor: int):
+    """The cameras at `factor` times the resolution whose factor x factor pixel blocks hold
+    each original pixel's sub-pixel rays (width, height, fx, fy, cx, cy all scaled)."""
+    out = []
+    for c in cams:
+        d = dict(c)
+        for k in ("width", "height"):
+            d[k] = int(c[k]) * factor
+        for k in ("fx", "fy", "cx", "cy"):
+            d[k] = np.float32(float(c[k]) * factor)
+        out.append(d)
+    return out
 
 
 def raygs_read_counters(plan, stream=None) -> dict:
