@@ -19,6 +19,10 @@
  *   - Camera-inside skip (Sec. 3.2, Eq. c): skip when c^2 = mu^T Sigma^-1 mu <= kappa.
  *   - Divergence (Sec. 3.2, Eq. Q_ray): tau = x^T Sigma^-1 mu / x^T Sigma^-1 x and
  *     D_ray = (tau x - mu)^T Sigma^-1 (tau x - mu), evaluated per pixel ray.
+ *   - GS divergence (Sec. 3.1), selected by the configuration instead of D_ray:
+ *     D_gs = (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), Sigma_pi = J Sigma J^T with J
+ *     the Jacobian of the pinhole projection at the mean, pi(x) the pixel centre.  There
+ *     is no camera-inside skip and no Eq. mip term for it (a MIP camera is refused).
  *   - Rendered opacity (Sec. 3, Eq. rend_opacity): omega = o exp(-D/2); it counts only
  *     when D <= kappa (equivalently omega >= p_min).
  *   - Rendering equation (Sec. 3, Eq. rendering): front-to-back compositing over the
@@ -58,7 +62,10 @@
 enum { CAM_FX = 0, CAM_FY, CAM_CX, CAM_CY, CAM_W, CAM_H, CAM_R = 6, CAM_T = 15,
        CAM_NEAR = 18, CAM_MIP = 19, CAM_LEN = 20 };
 /* configuration: p_min, t_stop, alpha_max, mip sigma^2 (pixel units) */
-enum { CFG_PMIN = 0, CFG_TSTOP, CFG_AMAX, CFG_MIPS2, CFG_LEN };
+/* CFG_DIV: 0 for the ray divergence D_ray (Eq. Q_ray), 1 for the GS divergence D_gs of
+ * Sec. 3.1 (EWA: Mahalanobis distance in pixel space under Sigma_pi = J Sigma J^T, J the
+ * Jacobian of the projection at the mean) */
+enum { CFG_PMIN = 0, CFG_TSTOP, CFG_AMAX, CFG_MIPS2, CFG_DIV, CFG_LEN };
 
 /* per-primitive output record of oracle_prepare (doubles) */
 enum {
@@ -294,6 +301,7 @@ typedef struct {
   double W[9];     /* whitening map S^-1 R_c^T, row-major: Sigma^-1 = W^T W */
   double m[3];     /* W mu */
   double c2, kappa, o, rgb[3], s[3], Rc[9];
+  double u[2], A[3]; /* GS: projected mean (pixels) and Sigma_pi^-1 = [[A0, A1], [A1, A2]] */
 } prim;
 
 static void prepare_one(int64_t i, const float *means, const float *log_scales,
@@ -330,6 +338,7 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
   for (int k = 0; k < 3; ++k)
     Rtmu[k] = g->Rc[k] * g->mu[0] + g->Rc[3 + k] * g->mu[1] + g->Rc[6 + k] * g->mu[2];
 
+  const int gs_div = (int)cfg[CFG_DIV] == 1;
   if ((int)cam[CAM_MIP]) {
     /* Eq. mip with the pixel-invariant Sigma^ = Sigma + lambda I */
     double mu2 = g->mu[0] * g->mu[0] + g->mu[1] * g->mu[1] + g->mu[2] * g->mu[2];
@@ -356,8 +365,36 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
     for (int j = 0; j < 3; ++j) g->W[3 * k + j] = g->Rc[3 * j + k] / g->s[k];
   for (int k = 0; k < 3; ++k) g->m[k] = Rtmu[k] / g->s[k];
   g->c2 = g->m[0] * g->m[0] + g->m[1] * g->m[1] + g->m[2] * g->m[2];
-  if (fabs(g->c2 - g->kappa) <= 1e-5 * g->kappa) g->border = 1;
-  if (!(g->c2 > g->kappa)) { g->status = 3; return; }
+  if (gs_div) {
+    /* Sec. 3.1: Sigma_pi = J Sigma J^T with J the Jacobian of pi(p) = (fx p_x / p_z + cx,
+     * fy p_y / p_z + cy) at the camera-frame mean; Sigma = R_c S^2 R_c^T */
+    double Sg[9];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double v = 0;
+        for (int k = 0; k < 3; ++k) v += g->Rc[3 * a + k] * s2[k] * g->Rc[3 * b + k];
+        Sg[3 * a + b] = v;
+      }
+    const double z = g->mu[2], fx = cam[CAM_FX], fy = cam[CAM_FY];
+    const double J[6] = {fx / z, 0.0, -fx * g->mu[0] / (z * z), 0.0, fy / z, -fy * g->mu[1] / (z * z)};
+    double P[4];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        double v = 0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) v += J[3 * a + i] * Sg[3 * i + j] * J[3 * b + j];
+        P[2 * a + b] = v;
+      }
+    const double det = P[0] * P[3] - P[1] * P[2];
+    g->A[0] = P[3] / det;
+    g->A[1] = -P[1] / det;
+    g->A[2] = P[0] / det;
+    g->u[0] = fx * g->mu[0] / z + cam[CAM_CX];
+    g->u[1] = fy * g->mu[1] / z + cam[CAM_CY];
+  } else {
+    if (fabs(g->c2 - g->kappa) <= 1e-5 * g->kappa) g->border = 1;
+    if (!(g->c2 > g->kappa)) { g->status = 3; return; }
+  }
 
   /* colour: direction from the camera centre C = -R^T t to the world-frame mean */
   double C[3], d[3], dn = 0;
@@ -388,6 +425,7 @@ int oracle_prepare(int64_t n, const float *means, const float *log_scales, const
                    const float *logits, const float *sh, int sh_degree, const double *cam,
                    const double *cfg, double *out) {
   if (n < 0 || sh_degree < 0 || sh_degree > 3) return 1;
+  if ((int)cfg[CFG_DIV] == 1 && (int)cam[CAM_MIP]) return 4; /* Eq. mip is a RayGS term */
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     prim g;
@@ -422,6 +460,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                   double *Tout, int32_t *ncontrib, int32_t *flags, uint64_t *sig,
                   int n_threads) {
   if (n < 0 || sh_degree < 0 || sh_degree > 3) return 1;
+  if ((int)cfg[CFG_DIV] == 1 && (int)cam[CAM_MIP]) return 4; /* Eq. mip is a RayGS term */
   int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
   if (!pix && n_pix != (int64_t)W * H) return 2;
 #ifdef _OPENMP
@@ -449,6 +488,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
 
   const double fx = cam[CAM_FX], fy = cam[CAM_FY], cx = cam[CAM_CX], cy = cam[CAM_CY];
   const double pmin = cfg[CFG_PMIN], tstop = cfg[CFG_TSTOP], amax = cfg[CFG_AMAX];
+  const int gs_div = (int)cfg[CFG_DIV] == 1;
 
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t p = 0; p < n_pix; ++p) {
@@ -460,14 +500,21 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
     uint64_t h = 1469598103934665603ull;
     for (int64_t k = 0; k < nv; ++k) {
       const prim *g = order[k];
-      double w[3];
-      for (int r = 0; r < 3; ++r) w[r] = g->W[3 * r] * x[0] + g->W[3 * r + 1] * x[1] + g->W[3 * r + 2] * x[2];
-      double num = g->m[0] * w[0] + g->m[1] * w[1] + g->m[2] * w[2]; /* x^T Si mu */
-      double den = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];          /* x^T Si x  */
-      double tau = num / den;
-      if (!(tau > 0)) continue;
-      double r0 = tau * w[0] - g->m[0], r1 = tau * w[1] - g->m[1], r2 = tau * w[2] - g->m[2];
-      double D = r0 * r0 + r1 * r1 + r2 * r2;
+      double D;
+      if (gs_div) {
+        /* Sec. 3.1: (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), pi(x) the pixel centre */
+        const double dx = (px + 0.5) - g->u[0], dy = (py + 0.5) - g->u[1];
+        D = g->A[0] * dx * dx + 2.0 * g->A[1] * dx * dy + g->A[2] * dy * dy;
+      } else {
+        double w[3];
+        for (int r = 0; r < 3; ++r) w[r] = g->W[3 * r] * x[0] + g->W[3 * r + 1] * x[1] + g->W[3 * r + 2] * x[2];
+        double num = g->m[0] * w[0] + g->m[1] * w[1] + g->m[2] * w[2]; /* x^T Si mu */
+        double den = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];          /* x^T Si x  */
+        double tau = num / den;
+        if (!(tau > 0)) continue;
+        double r0 = tau * w[0] - g->m[0], r1 = tau * w[1] - g->m[1], r2 = tau * w[2] - g->m[2];
+        D = r0 * r0 + r1 * r1 + r2 * r2;
+      }
       double om = g->o * exp(-0.5 * D);
       if (fabs(om - pmin) <= 1e-6) fl |= FLAG_CUTOFF;
       if (!(D <= g->kappa)) continue;

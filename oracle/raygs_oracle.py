@@ -18,7 +18,8 @@ _lib = None
 OG = dict(STATUS=0, KEY=1, MU=slice(2, 5), C2=5, KAPPA=6, O=7, RGB=slice(8, 11),
           S=slice(11, 14), RC=slice(14, 23), BORDER=23, LEN=24)
 
-DEFAULT_CFG = dict(p_min=1.0 / 255.0, t_stop=1e-4, alpha_max=0.99, mip_sigma2=0.1)
+# divergence: 0 the ray divergence (Eq. Q_ray), 1 the GS divergence of Sec. 3.1
+DEFAULT_CFG = dict(p_min=1.0 / 255.0, t_stop=1e-4, alpha_max=0.99, mip_sigma2=0.1, divergence=0)
 
 FLAG_CUTOFF, FLAG_STOP, FLAG_BORDER = 1, 2, 4
 
@@ -84,7 +85,7 @@ def cfg_array(cfg: dict | None = None) -> np.ndarray:
     c = dict(DEFAULT_CFG)
     if cfg:
         c.update(cfg)
-    return np.array([c["p_min"], c["t_stop"], c["alpha_max"], c["mip_sigma2"]], dtype=np.float64)
+    return np.array([c["p_min"], c["t_stop"], c["alpha_max"], c["mip_sigma2"], c["divergence"]], dtype=np.float64)
 
 
 def _scene_arrays(scene: dict):

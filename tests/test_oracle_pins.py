@@ -485,3 +485,104 @@ def test_golden_small_scene_regression(oracle_lib):
     np.testing.assert_allclose(out["rgb"], rgb, rtol=0, atol=1e-12)
     np.testing.assert_allclose(out["T"], T, rtol=0, atol=1e-12)
     assert np.array_equal(out["flags"].astype(np.int32), flags)
+
+
+# ---------------------------------------------------------------- GS divergence (Sec. 3.1)
+
+def _gs_single_T(o, D, kappa):
+    om = np.where(D <= kappa, np.minimum(o * np.exp(-D / 2), 0.99), 0.0)
+    return 1.0 - om
+
+
+def test_gs_isotropic_on_axis(oracle_lib):
+    """Sigma = s^2 I at mu = (0, 0, z0): J = diag(fx/z0, fy/z0) (third column zero), so by hand
+    D_gs = (dx z0 / (fx s))^2 + (dy z0 / (fy s))^2 with (dx, dy) the offset of the pixel centre
+    from the principal point.  fx != fy catches swapped Jacobian rows."""
+    z0, s, logit = 2.5, 0.04, 0.7
+    sc = single([0, 0, z0], np.log([s] * 3), [1, 0, 0, 0], logit, [1, 1, 1])
+    cam = scenes.make_camera(40, 36, 300.0, 220.0, 20.0, 18.0)
+    out = oracle_lib.render(sc, cam, cfg=dict(divergence=1))
+    j, i = np.divmod(np.arange(40 * 36), 40)
+    sf = math.exp(float(np.float32(np.log(s))))
+    D = ((i + 0.5 - 20.0) * z0 / (300.0 * sf)) ** 2 + ((j + 0.5 - 18.0) * z0 / (220.0 * sf)) ** 2
+    o = 1.0 / (1.0 + math.exp(-float(np.float32(logit))))
+    kappa = -2 * math.log(PMIN / o)
+    np.testing.assert_allclose(out["T"], _gs_single_T(o, D, kappa), rtol=1e-12, atol=1e-15)
+    assert np.count_nonzero(out["ncontrib"]) > 100
+
+
+def _project(p, f, c):
+    return np.array([f[0] * p[0] / p[2] + c[0], f[1] * p[1] / p[2] + c[1]])
+
+
+def test_gs_numeric_jacobian(oracle_lib):
+    """Random rotated, anisotropic primitives seen by a rotated camera.  Independent
+    restatement: Sigma from scipy's rotation of the quaternion, the camera-frame mean from
+    the camera's R and t, J of the projection by central differences (exact to ~1e-10 for a
+    rational map), Sigma_pi = J Sigma J^T and D by np.linalg.solve.  A transposed J, a dropped
+    off-axis column or a wrong world-to-camera step fails it."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(21)
+    R, t = scenes.look_at([0.3, -0.2, -4.0], [0.0, 0.1, 0.0])
+    cam = scenes.make_camera(48, 40, 260.0, 240.0, 22.5, 21.0, R=R, t=t)
+    Rf, tf = cam["R"].astype(np.float64), cam["t"].astype(np.float64)
+    f, c = (260.0, 240.0), (22.5, 21.0)
+    checked = 0
+    for _ in range(12):
+        mu_w = rng.uniform(-0.6, 0.6, 3).astype(np.float32)
+        ls = np.log(rng.uniform(0.05, 0.3, 3)).astype(np.float32)
+        q = rand_rot(rng).astype(np.float32)
+        sc = single(mu_w, ls, q, 2.0, [1, 1, 1])
+        out = oracle_lib.render(sc, cam, cfg=dict(divergence=1))
+        mu = Rf @ mu_w.astype(np.float64) + tf
+        Rq = Rot.from_quat(q.astype(np.float64)[[1, 2, 3, 0]]).as_matrix()
+        Sw = Rq @ np.diag(np.exp(2 * ls.astype(np.float64))) @ Rq.T
+        Sc = Rf @ Sw @ Rf.T
+        J = np.zeros((2, 3))
+        for k in range(3):
+            h = 1e-6 * abs(mu[2])
+            e = np.zeros(3); e[k] = h
+            J[:, k] = (_project(mu + e, f, c) - _project(mu - e, f, c)) / (2 * h)
+        Sp = J @ Sc @ J.T
+        u = _project(mu, f, c)
+        j, i = np.divmod(np.arange(48 * 40), 48)
+        dlt = np.stack([i + 0.5 - u[0], j + 0.5 - u[1]])
+        D = np.einsum("ip,ip->p", dlt, np.linalg.solve(Sp, dlt))
+        o = 1.0 / (1.0 + math.exp(-float(np.float32(2.0))))
+        kappa = -2 * math.log(PMIN / o)
+        keep = np.abs(D - kappa) > 1e-6 * kappa
+        np.testing.assert_allclose(out["T"][keep], _gs_single_T(o, D, kappa)[keep], rtol=1e-7, atol=1e-9)
+        checked += np.count_nonzero(out["ncontrib"][keep])
+    assert checked > 500
+
+
+def test_gs_approaches_ray_for_small_far_primitives(oracle_lib):
+    """Sec. 3.1 vs 3.2: the EWA linearisation is exact in the limit of a primitive that is
+    small against its distance and near the principal ray, where D_gs and D_ray agree.  For an
+    isotropic primitive on the axis, by hand, D_ray = D_gs / (1 + |x_n|^2) with x_n the
+    normalised image coordinate, so the images differ by O(field of view^2)."""
+    rng = np.random.default_rng(5)
+    cam = scenes.make_camera(32, 32, 4000.0, 4000.0)
+    for _ in range(6):
+        mu = np.array([*rng.uniform(-0.02, 0.02, 2), 50.0], np.float32)
+        sc = single(mu, np.log(rng.uniform(0.02, 0.05, 3)), rand_rot(rng), 1.5, [1, 1, 1])
+        a = oracle_lib.render(sc, cam)
+        b = oracle_lib.render(sc, cam, cfg=dict(divergence=1))
+        assert np.count_nonzero(a["ncontrib"]) > 50
+        both = (a["ncontrib"] > 0) == (b["ncontrib"] > 0)
+        np.testing.assert_allclose(b["T"][both], a["T"][both], atol=1e-3)
+        # where one support edge passes the pixel and the other does not, omega ~ p_min
+        assert np.all(np.abs(b["T"] - a["T"])[~both] <= 1.05 * PMIN)
+        assert np.count_nonzero(~both) <= 0.05 * np.count_nonzero(a["ncontrib"])
+
+
+def test_gs_refuses_mip_and_skips_no_inside_camera(oracle_lib):
+    """D_gs has no camera-inside skip: a primitive whose RayGS support holds the camera
+    centre (c^2 <= kappa) is culled by RayGS but still splatted by GS.  Eq. mip is a RayGS
+    term: a MIP camera with the GS divergence is refused."""
+    sc = single([0, 0, 0.5], np.log([0.6] * 3), [1, 0, 0, 0], 3.0, [1, 1, 1])
+    cam = scenes.make_camera(16, 16, 20.0, 20.0)
+    assert np.all(oracle_lib.render(sc, cam)["ncontrib"] == 0)
+    assert np.any(oracle_lib.render(sc, cam, cfg=dict(divergence=1))["ncontrib"] > 0)
+    with pytest.raises(RuntimeError):
+        oracle_lib.render(sc, dict(cam, mip=True), cfg=dict(divergence=1))
