@@ -303,6 +303,7 @@ def run_ours(args, world, rank, local):
     # streams, so that one batch's rasteriser overlaps the next batch's vertex stage and
     # binning.  Every step is still one complete 16-view batch.
     plans = [(r, stream)]
+    plan_outputs = []  # the captured graphs write these: alive as long as their plans
     for _ in range(max(1, args.in_flight) - 1):
         r2 = raygs.Renderer(cams, n, device=dev, capacity=r.capacity, tile_w=r.cfg.tile_w, tile_h=r.cfg.tile_h,
                             batch_records=r.cfg.batch_records)
@@ -314,6 +315,8 @@ def run_ours(args, world, rank, local):
             raygs.raygs_graph_capture(r2.plan, sc, *o2, s2)
         s2.synchronize()
         plans.append((r2, s2))
+        plan_outputs.append(o2)
+        r2 = o2 = None
 
     def headline(nplans, steps):
         """Time `steps` graph launches spread round-robin over the first `nplans` plans."""
@@ -413,6 +416,11 @@ def run_ours(args, world, rank, local):
     if not args.no_backward:
         line["fwd_bwd"] = fwd_bwd_ms_per_view(args, dev)
     if not args.no_precision:
+        del plans[1:]
+        plan_outputs.clear()
+        torch.cuda.empty_cache()
+        line["gs_vs_raygs"] = dict(stereo_batch=divergence_ab(st, cams, n, r.cfg, r.capacity, dev),
+                                   plain_720p=divergence_ab_720p(r.cfg, dev))
         line["precision_storage"] = precision_storage(args, dev)
         line["antialiasing"] = antialiasing(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -420,6 +428,63 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def divergence_ab(st, cams, n, cfg, capacity, dev):
+    """The stereo batch rendered with the GS divergence of Sec. 3.1 (EWA) and with RayGS's
+    D_ray, on the same kernels, tile shape and scene: time of one forward batch (vertex
+    stage, binning and rasteriser run back to back) of each, per-stage times, the instance
+    and evaluation counts, and the GS image against the RayGS one (max-abs, mean-abs, PSNR
+    for a unit range)."""
+    import torch
+    from paper_2503_18682_gb300 import raygs
+    sc = raygs.make_scene(st)
+    out, imgs = {}, {}
+    for name, div in (("raygs", 0), ("gs", 1)):
+        r = raygs.Renderer(cams, n, device=dev, capacity=capacity, tile_w=cfg.tile_w, tile_h=cfg.tile_h,
+                           batch_records=cfg.batch_records, divergence=div)
+        rgb, T, nc = r.forward(st)  # regrows the plan when GS needs more instances
+        ctr = dict(r.last_counters)
+        evals, comps = r.counted_render(rgb, T, nc)
+        stages = [lambda: raygs.raygs_preprocess(r.plan, sc), lambda: raygs.raygs_bin_sort(r.plan),
+                  lambda: raygs.raygs_render(r.plan, rgb, T, nc)]
+        for _ in range(2):
+            for f in stages:
+                f()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        reps = 5
+        acc = [0.0, 0.0, 0.0]
+        for _ in range(reps):
+            for i, f in enumerate(stages):
+                ev[i].record()
+                f()
+            ev[3].record()
+            ev[3].synchronize()
+            for i in range(3):
+                acc[i] += ev[i].elapsed_time(ev[i + 1])
+        ms = [a / reps for a in acc]
+        out[name] = dict(forward_ms=sum(ms), preprocess_ms=ms[0], bin_sort_ms=ms[1], render_ms=ms[2],
+                         n_visible=ctr["n_visible"], n_instances=ctr["n_instances"], evaluated_pairs=evals,
+                         composited_pairs=comps)
+        imgs[name] = rgb.clone()
+        del r, rgb, T, nc
+        torch.cuda.empty_cache()
+    d = (imgs["gs"] - imgs["raygs"]).double()
+    mse = float((d ** 2).mean())
+    out["gs_vs_raygs_image"] = dict(max_abs=float(d.abs().max()), mean_abs=float(d.abs().mean()),
+                                    psnr_db=(99.0 if mse == 0 else -10 * np.log10(mse)))
+    out["gs_speedup"] = out["raygs"]["forward_ms"] / out["gs"]["forward_ms"]
+    return out
+
+
+def divergence_ab_720p(cfg, dev):
+    """divergence_ab on the 720p workload without the MIP term (500k primitives, one view
+    whose primitives all lie in front of the camera, none near it)."""
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene, cams = scenes.workload_mip_720p()
+    cams = [dict(c, mip=False) for c in cams]
+    n = int(scene["means"].shape[0])
+    return divergence_ab(raygs.scene_to_device(scene, dev), cams, n, cfg, None, dev)
 
 
 def antialiasing(args, dev):

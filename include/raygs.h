@@ -77,6 +77,14 @@ typedef struct {
   int32_t mip;
 } raygs_camera;
 
+/* The divergence D that weighs a primitive at a pixel, omega = o exp(-D/2).
+ *   RAYGS_DIV_RAY: D_ray of Sec. 3.2 (Eq. Q_ray), the Mahalanobis distance of the density
+ *                  maximum along the pixel ray, with the camera-inside skip of Eq. c.
+ *   RAYGS_DIV_GS:  D_gs of Sec. 3.1, the Mahalanobis distance of the pixel centre from the
+ *                  projected mean under Sigma_pi = J Sigma J^T (EWA splatting, J the
+ *                  Jacobian of the pinhole projection at the mean); no Eq. c skip. */
+typedef enum { RAYGS_DIV_RAY = 0, RAYGS_DIV_GS = 1 } raygs_divergence;
+
 /* Renderer settings.  raygs_config_default() fills the documented defaults. */
 typedef struct {
   float p_min;            /* support cut-off of Eq. support (default 1/255) */
@@ -92,6 +100,8 @@ typedef struct {
   int32_t enable_backward; /* 1: reserve workspace for raygs_render_backward (default 0) */
   int32_t batch_records;  /* records the rasteriser stages in shared memory per thread and
                              batch: 1 (default) or 2 */
+  int32_t divergence;     /* raygs_divergence: RAYGS_DIV_RAY (default) or RAYGS_DIV_GS.  GS
+                             refuses enable_backward and cameras with mip != 0 (INVALID_ARG) */
 } raygs_config;
 
 /* Device-side counters of the last preprocess / bin_sort / render sequence. */
@@ -165,7 +175,8 @@ int64_t raygs_plan_num_tiles(const raygs_plan *plan);           /* screen tiles,
  * Per-primitive vertex stage for every view (Sec. 3 activation; Sec. 3.2 Eq. c skip;
  * Sec. 5 Eq. mip; Sec. 4.1 and App. A.1-A.3 quad V_ray -> screen tile rectangle; the
  * per-pixel factors of the fragment formula of Sec. 4.2 / App. A.4; colour from SH).
- * Reads the scene, writes per-(primitive, view) depth keys, tile rectangles and 64-byte
+ * With RAYGS_DIV_GS the records instead hold Sigma_pi^-1 of Sec. 3.1 and the tile
+ * rectangle bounds the screen ellipse of the EWA support.  Reads the scene, writes per-(primitive, view) depth keys, tile rectangles and 64-byte
  * pixel records into the workspace.  Requires a bound plan and scene->n == n_gaussians.
  */
 raygs_status raygs_preprocess(raygs_plan *plan, const raygs_scene *scene, void *stream);

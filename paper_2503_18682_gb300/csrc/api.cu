@@ -42,6 +42,7 @@ void raygs_config_default(raygs_config *cfg) {
   cfg->fp64_degenerate = 1;
   cfg->degenerate_ratio = 1e3f;
   cfg->enable_backward = 0;
+  cfg->divergence = RAYGS_DIV_RAY;
   cfg->batch_records = 1;
 }
 

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
         if ((hit & (1u << k)) && pos < last[k]) {
           any = true;
           const float4 Cc = s_C[j], Dd = s_D[j];
-          const float raw = pixel_opacity(Cc, q[k], r[k]);
+          const float raw = pixel_opacity(Cc, q[k], r[k], 1.f);
           const bool clamped = raw > P.alpha_max;
           const float om = clamped ? P.alpha_max : raw;
           const float onem = 1.f - om;

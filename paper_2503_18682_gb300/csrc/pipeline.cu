@@ -38,7 +38,8 @@ bool config_valid(const raygs_config &cfg) {
   return tile_ok && cfg.p_min > 0.f && cfg.p_min < 1.f && cfg.t_stop >= 0.f && cfg.t_stop < 1.f &&
          cfg.alpha_max > 0.f && cfg.alpha_max < 1.f && cfg.mip_sigma2 >= 0.f && cfg.degenerate_ratio > 1.f &&
          cfg.fp64_degenerate >= 0 && cfg.fp64_degenerate <= 2 && (cfg.enable_backward == 0 || cfg.enable_backward == 1) &&
-         (cfg.batch_records == 1 || cfg.batch_records == 2);
+         (cfg.batch_records == 1 || cfg.batch_records == 2) && (cfg.divergence == 0 || cfg.divergence == 1) &&
+         !(cfg.divergence == 1 && cfg.enable_backward);
 }
 
 bool camera_valid(const raygs_camera &c) {
@@ -122,6 +123,7 @@ bool plan_views(const raygs_camera *cams, int n_views, const raygs_config &cfg, 
   tiles = 0; trows = 0; pixels = 0; max_tiles_x = 0;
   for (int v = 0; v < n_views; ++v) {
     if (!camera_valid(cams[v])) return false;
+    if (cfg.divergence == 1 && cams[v].mip) return false;  // Eq. mip is a RayGS term
     fill_devcam(cams[v], cfg, dc[v]);
     if (dc[v].tiles_x > kMaxTilesX) return false;
     dc[v].tile_base = int(tiles);
@@ -156,6 +158,7 @@ cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st) {
   P.mip_sigma2 = w.cfg.mip_sigma2;
   P.degenerate_ratio = w.cfg.degenerate_ratio;
   P.fp64_degenerate = w.cfg.fp64_degenerate;
+  P.divergence = w.cfg.divergence;
   P.tile_w = w.cfg.tile_w;
   P.tile_h = w.cfg.tile_h;
   P.depth_key = w.at<uint32_t>(w.L.depth);
@@ -309,6 +312,7 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
   P.rec = w.at<Rec>(w.L.rec);
   P.t_stop = w.cfg.t_stop;
   P.alpha_max = w.cfg.alpha_max;
+  P.qmix = w.cfg.divergence == 1 ? 0.f : 1.f;
   P.rgb = rgb;
   P.Tf = T_final;
   P.ncontrib = n_contrib;

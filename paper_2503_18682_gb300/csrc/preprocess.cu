@@ -1,5 +1,5 @@
-// Per-primitive vertex stage (Sec. 3, Sec. 3.2, Sec. 4.1, Sec. 5 of the paper) for every
-// view of a batch.  One thread per primitive loops over the views; attributes are staged
+// Per-primitive vertex stage (Sec. 3, Sec. 3.2, Sec. 4.1, Sec. 5 of the paper; Sec. 3.1 for
+// the GS divergence) for every view of a batch.  One thread per primitive loops over the views; attributes are staged
 // once per CTA with 16-byte coalesced loads and converted to float32 in shared memory.
 //
 // Outputs per (view v, primitive g), index v*N + g:
@@ -34,6 +34,34 @@ template <typename T>
 __device__ __forceinline__ bool outside_frustum(const T mu[3], T rad, const DevCam &cam) {
   return mu[0] - T(cam.xmin) * mu[2] < -rad * T(cam.fn[0]) || T(cam.xmax) * mu[2] - mu[0] < -rad * T(cam.fn[1]) ||
          mu[1] - T(cam.ymin) * mu[2] < -rad * T(cam.fn[2]) || T(cam.ymax) * mu[2] - mu[1] < -rad * T(cam.fn[3]);
+}
+
+// Inclusive tile rectangle of the pixels whose centres lie in the screen box [xmn, xmx] x
+// [ymn, ymx] (with a small conservative margin), or of the whole view when `full`.
+// Returns false when the box holds no pixel centre of the view.
+__device__ __forceinline__ bool tile_rect(bool full, float xmn, float xmx, float ymn, float ymx, const DevCam &cam,
+                                          int tile_w, int tile_h, StageOut &out) {
+  int i0, i1, j0, j1;
+  if (full) {
+    i0 = 0; j0 = 0; i1 = cam.W - 1; j1 = cam.H - 1;
+  } else {
+    if (!(xmn <= xmx) || !(ymn <= ymx)) return false;  // empty or NaN
+    const float lim = 1.0e8f;
+    float mgx = 1e-3f + 1e-5f * fmaxf(fabsf(xmn), fabsf(xmx));
+    float mgy = 1e-3f + 1e-5f * fmaxf(fabsf(ymn), fabsf(ymx));
+    // pixel centre i + 0.5 inside [xmn, xmx] (with a small conservative margin)
+    float fi0 = ceilf(fminf(fmaxf(xmn - 0.5f - mgx, -lim), lim));
+    float fi1 = floorf(fminf(fmaxf(xmx - 0.5f + mgx, -lim), lim));
+    float fj0 = ceilf(fminf(fmaxf(ymn - 0.5f - mgy, -lim), lim));
+    float fj1 = floorf(fminf(fmaxf(ymx - 0.5f + mgy, -lim), lim));
+    fi0 = fmaxf(fi0, 0.f); fj0 = fmaxf(fj0, 0.f);
+    fi1 = fminf(fi1, float(cam.W - 1)); fj1 = fminf(fj1, float(cam.H - 1));
+    if (fi0 > fi1 || fj0 > fj1) return false;
+    i0 = int(fi0); i1 = int(fi1); j0 = int(fj0); j1 = int(fj1);
+  }
+  out.tx0 = i0 / tile_w; out.tx1 = i1 / tile_w;
+  out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
+  return true;
 }
 
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
@@ -202,28 +230,79 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
       }
     }
   }
-  int i0, i1, j0, j1;
-  if (full) {
-    i0 = 0; j0 = 0; i1 = cam.W - 1; j1 = cam.H - 1;
-  } else {
-    if (!(xmn <= xmx) || !(ymn <= ymx)) return false;  // empty or NaN
-    const float lim = 1.0e8f;
-    float mgx = 1e-3f + 1e-5f * fmaxf(fabsf(xmn), fabsf(xmx));
-    float mgy = 1e-3f + 1e-5f * fmaxf(fabsf(ymn), fabsf(ymx));
-    // pixel centre i + 0.5 inside [xmn, xmx] (with a small conservative margin)
-    float fi0 = ceilf(fminf(fmaxf(xmn - 0.5f - mgx, -lim), lim));
-    float fi1 = floorf(fminf(fmaxf(xmx - 0.5f + mgx, -lim), lim));
-    float fj0 = ceilf(fminf(fmaxf(ymn - 0.5f - mgy, -lim), lim));
-    float fj1 = floorf(fminf(fmaxf(ymx - 0.5f + mgy, -lim), lim));
-    fi0 = fmaxf(fi0, 0.f); fj0 = fmaxf(fj0, 0.f);
-    fi1 = fminf(fi1, float(cam.W - 1)); fj1 = fminf(fj1, float(cam.H - 1));
-    if (fi0 > fi1 || fj0 > fj1) return false;
-    i0 = int(fi0); i1 = int(fi1); j0 = int(fj0); j1 = int(fj1);
-  }
-  out.tx0 = i0 / tile_w; out.tx1 = i1 / tile_w;
-  out.ty0 = j0 / tile_h; out.ty1 = j1 / tile_h;
+  return tile_rect(full, xmn, xmx, ymn, ymx, cam, tile_w, tile_h, out);
+}
 
-  return true;
+// GS vertex stage (Sec. 3.1) in precision T: Sigma_pi = J Sigma J^T with J the Jacobian of
+// the projection at the camera-frame mean mu, and records for D_gs = delta^T Sigma_pi^-1
+// delta.  With M = J R_c S (2x3, rows m0, m1), Sigma_pi = M M^T and det Sigma_pi =
+// |m0 x m1|^2 (Cauchy-Binet).  Since m_i = S R_c^T j_i and j0 x j1 = (fx fy / z^2) mu / z,
+// m0 x m1 = (s0 s1 s2 fx fy / z^3) S^-1 R_c^T mu, so det Sigma_pi = (s0 s1 s2 fx fy / z^3)^2 c^2
+// with c^2 = mu^T Sigma^-1 mu: a sum of squares, free of the cancellation that the
+// 2x2 determinant (or the cross product) suffers for thin disks seen edge-on.  The record holds
+// the upper Cholesky factor G of A = Sigma_pi^-1 (G^T G = A, G10 = 0), h = 0,
+// kp = 1 / kappa and c2h = log2(e) / 2, so the rasteriser's test reads |G delta|^2 <= kappa
+// and its exponent D_gs log2(e) / 2.  The support is the ellipse delta^T A delta <= kappa.
+// There is no camera-inside skip (Eq. c) and no Eq. mip term.
+template <typename T>
+__device__ bool gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
+                              int tile_w, int tile_h, StageOut &out) {
+  T kappa = T(2) * t_log(o / T(p_min));
+  if (!(kappa > T(0))) return false;
+  T Rc[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Rc[3 * i + j] = T(cam.R[3 * i]) * Rp[j] + T(cam.R[3 * i + 1]) * Rp[3 + j] +
+                      T(cam.R[3 * i + 2]) * Rp[6 + j];
+  // rows of J: (fx / z) (e_0 - (x / z) e_2) and (fy / z) (e_1 - (y / z) e_2)
+  const T iz = T(1) / mu[2];
+  const T ax = mu[0] * iz, ay = mu[1] * iz;
+  const T jx = T(cam.fx) * iz, jy = T(cam.fy) * iz;
+  T m0[3], m1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m0[k] = jx * (Rc[k] - ax * Rc[6 + k]) * s[k];
+    m1[k] = jy * (Rc[3 + k] - ay * Rc[6 + k]) * s[k];
+  }
+  const T P00 = m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2];
+  const T P01 = m0[0] * m1[0] + m0[1] * m1[1] + m0[2] * m1[2];
+  const T P11 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+  T c2 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T mk = (Rc[k] * mu[0] + Rc[3 + k] * mu[1] + Rc[6 + k] * mu[2]) / s[k];
+    c2 += mk * mk;
+  }
+  const T sd = s[0] * s[1] * s[2] * jx * jy * iz;
+  const T det = sd * sd * c2;  // det Sigma_pi
+  if (!(det > T(0)) || !(P00 > T(0)) || !(P11 > T(0))) return false;
+  // A = Sigma_pi^-1 = [[P11, -P01], [-P01, P00]] / det; G00 = sqrt(A00), G01 = A01 / G00,
+  // G11 = sqrt(det A) / G00 with det A = 1 / det Sigma_pi
+  const T idet = T(1) / det;
+  const T A00 = P11 * idet, A01 = -P01 * idet, A11 = P00 * idet;
+  const T g00 = t_sqrt(A00);
+  out.G[0] = float(g00);
+  out.G[1] = float(A01 / g00);
+  out.G[2] = 0.f;
+  out.G[3] = float(T(1) / (t_sqrt(det) * g00));
+  out.h[0] = 0.f;
+  out.h[1] = 0.f;
+  out.kp = float(T(1) / kappa);
+  out.c2h = float(0.5 * 1.4426950408889634);
+  out.lo2o = float(t_log(o) * T(1.4426950408889634));
+  out.illcond = false;
+  // support ellipse, normalised by kappa; its bounding box half-widths sqrt(kappa Sigma_pi)
+  const T ik = T(1) / kappa;
+  out.dc0 = 0.f; out.dc1 = 0.f;
+  out.M00 = float(A00 * ik); out.M01 = float(A01 * ik); out.M11 = float(A11 * ik);
+  out.rho = float(kappa);
+  out.det = float(idet * ik * ik);
+  const T ucx = jx * mu[0] + T(cam.cx), ucy = jy * mu[1] + T(cam.cy);
+  const T hx = t_sqrt(kappa * T(1.001) * P00), hy = t_sqrt(kappa * T(1.001) * P11);
+  return tile_rect(false, float(ucx - hx), float(ucx + hx), float(ucy - hy), float(ucy + hy), cam, tile_w,
+                   tile_h, out);
 }
 
 __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, const DevCam &cam,
@@ -349,7 +428,9 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
             if (cam.mip)
               s2 += P.mip_sigma2 * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) / (cam.fx * cam.fy);
             const float rad = sk * sqrtf(s2) * 1.01f + 1e-5f * (fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2])) + 1e-5f;
-            keep = !outside_frustum<float>(mu, rad, cam);
+            // the GS support is the linearised projection, not bounded by the sphere's
+            // cone: its exact screen box decides in the full stage
+            keep = P.divergence == 1 || !outside_frustum<float>(mu, rad, cam);
           }
         }
         if (!keep) P.depth_key[idx] = kCulled;
@@ -379,7 +460,10 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
 #pragma unroll
       for (int k = 0; k < 9; ++k) Rp[k] = s_R[9 * tt + k];
       StageOut so;
-      if (!view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+      const bool vis = P.divergence == 1
+                           ? gs_view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.tile_w, P.tile_h, so)
+                           : view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so);
+      if (!vis) {
         P.depth_key[idx] = kCulled;
         continue;
       }
@@ -424,7 +508,10 @@ __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
     const double mu[3] = {double(muc[0].hi) + double(muc[0].lo), double(muc[1].hi) + double(muc[1].lo),
                           double(muc[2].hi) + double(muc[2].lo)};
     StageOut so;
-    if (!view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so)) {
+    const bool vis = P.divergence == 1 ? gs_view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.tile_w, P.tile_h, so)
+                                       : view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w,
+                                                            P.tile_h, so);
+    if (!vis) {
       P.depth_key[idx] = kCulled;
       continue;
     }

@@ -95,9 +95,10 @@ __device__ __forceinline__ uint32_t eval_pixels(const float4 &A, const float4 &B
   return hit;
 }
 
-// Rendered opacity before the clamp (fragment formula + Eq. rend_opacity).
-__device__ __forceinline__ float pixel_opacity(const float4 &C, float q, float r) {
-  const float E = C.y * __fdividef(q, q + r);
+// Rendered opacity before the clamp (fragment formula + Eq. rend_opacity).  qmix = 1 for
+// D_ray; the D_gs records (h = 0, so r = 1) take qmix = 0 and give E = c2h q.
+__device__ __forceinline__ float pixel_opacity(const float4 &C, float q, float r, float qmix) {
+  const float E = C.y * __fdividef(q, fmaf(q, qmix, r));
   return ex2_approx(C.z - E);
 }
 

@@ -155,6 +155,7 @@ struct PrepParams {
   const DevCam *cams;
   float p_min, mip_sigma2, degenerate_ratio;
   int fp64_degenerate;
+  int divergence;  // 0: D_ray (Eq. Q_ray); 1: D_gs (Sec. 3.1)
   int tile_w, tile_h;
   uint32_t *depth_key;
   uint2 *rect;
@@ -252,6 +253,7 @@ struct RenderParams {
   const uint32_t *pairs;
   const Rec *rec;
   float t_stop, alpha_max;
+  float qmix;  // 1: D_ray fragment formula, D ~ q / (q + r); 0: D_gs, D ~ q (records with h = 0)
   float *rgb;
   float *Tf;
   int *ncontrib;

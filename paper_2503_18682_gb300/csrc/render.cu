@@ -10,6 +10,8 @@
 //   contributes iff y2 > 0 and kp q - r <= 0          (D <= kappa, Eq. support)
 //   D log2(e)/2 = c2h q / (q + r)                     (fragment formula)
 //   omega = min(alpha_max, 2^(log2 o - D log2(e)/2))
+// With the GS divergence of Sec. 3.1 the records carry h = 0 and G with G^T G = Sigma_pi^-1,
+// so that r = 1, the test reads q <= kappa and D log2(e)/2 = c2h q (qmix = 0 below).
 // A thread's PX pixels lie on one tile row, interleaved with the other threads of that
 // row (columns lx, lx + QX, lx + 2 QX, ...), so that a footprint covering a range of
 // columns hits the same pixel slots k in every lane of the row and the per-slot
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           if (hit & (1u << k)) {
-            const float al = fminf(P.alpha_max, pixel_opacity(Cc, q[k], r[k]));
+            const float al = fminf(P.alpha_max, pixel_opacity(Cc, q[k], r[k], P.qmix));
             const float w = al * T[k];
             const float Tn = T[k] - w;
             if (Tn < P.t_stop) {

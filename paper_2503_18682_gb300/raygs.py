@@ -34,7 +34,8 @@ class Config(C.Structure):
     _fields_ = [("p_min", C.c_float), ("t_stop", C.c_float), ("alpha_max", C.c_float),
                 ("mip_sigma2", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("fp64_degenerate", C.c_int32), ("degenerate_ratio", C.c_float),
-                ("enable_backward", C.c_int32), ("batch_records", C.c_int32)]
+                ("enable_backward", C.c_int32), ("batch_records", C.c_int32),
+                ("divergence", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -369,6 +370,8 @@ class Renderer:
         torch = _torch()
         if self.plan is not None:
             raygs_plan_destroy(self.plan)
+            self.plan = None
+        self._ws = None  # release the old workspace before sizing the new one
         self.plan = raygs_plan_create(self.cams, self.n, self.capacity, self.cfg)
         nb = raygs_plan_workspace_bytes(self.plan)
         self._ws = torch.empty(nb, dtype=torch.uint8, device=self.device)

@@ -43,6 +43,32 @@ def assert_parity(stats, tol=TOL):
     assert stats["max_err"] <= tol and stats["max_err_T"] <= tol, stats
 
 
+def allowed_in_sample(n_sampled, frac=EXCL_FRAC, p_fail=1e-3):
+    """Excluded pixels a uniform sample of n_sampled pixels may hold when the image's rate is
+    at most `frac`: the smallest k with P(Poisson(frac n_sampled) > k) < p_fail.  A sample of
+    1,024 pixels allows 2 and catches only rates well above 0.01% (a true rate of 0.5% fails
+    it with probability 0.88)."""
+    import math
+    lam = frac * n_sampled
+    k, term, cdf = 0, math.exp(-lam), math.exp(-lam)
+    while 1.0 - cdf >= p_fail:
+        k += 1
+        term *= lam / k
+        cdf += term
+    return k
+
+
+def assert_parity_sampled(stats_list, tol=TOL):
+    """Sampled pixels of several views, pooled: no unflagged pixel off by more than tol,
+    and no more flagged exclusions than allowed_in_sample grants the pooled sample."""
+    n = sum(s["n"] for s in stats_list)
+    excl = sum(s["n_excluded"] for s in stats_list)
+    for s in stats_list:
+        assert s["n_unexplained"] == 0, s
+        assert s["max_err"] <= tol and s["max_err_T"] <= tol, s
+    assert excl <= allowed_in_sample(n), (excl, n, stats_list)
+
+
 def sample_pixels(cam, n, seed):
     rng = np.random.default_rng(seed)
     W, H = cam["width"], cam["height"]
