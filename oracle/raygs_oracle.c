@@ -14,6 +14,13 @@
  *   - Anti-aliasing (Sec. 5, Eq. mip): Sigma^ = Sigma + lambda I with the pixel-invariant
  *     lambda = sigma^2 * tau_bar^2 / (fx fy), tau_bar = |mu| (tau of the unit ray through the
  *     mean), and the opacity modulated by sqrt(|Sigma| c^2 / (|Sigma^| c^^2)).
+ *   - Exact pixel-dependent anti-aliasing (Sec. 5 and its appendix derivation of P_MIP),
+ *     camera mip = 2: per unit pixel ray x, Sigma^_x = Sigma + sigma_x^2 tau(x)^2 I with
+ *     tau(x) the ray's maximum-density distance under Sigma and sigma_x^2 = sigma^2
+ *     cos^3(theta) / (fx fy) the pixel's area at unit distance along the ray;
+ *     omega = o m(x) exp(-D_ray(x; mu, Sigma^_x) / 2) with the modulation
+ *     m(x) = sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x)), counted when
+ *     omega >= p_min.  Camera-inside skip and kappa as for the plain primitive.
  *   - Support cut-off (Sec. 3, Eq. support): kappa = -2 log(p_min / o); a primitive with
  *     kappa <= 0 is skipped.
  *   - Camera-inside skip (Sec. 3.2, Eq. c): skip when c^2 = mu^T Sigma^-1 mu <= kappa.
@@ -339,7 +346,7 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
     Rtmu[k] = g->Rc[k] * g->mu[0] + g->Rc[3 + k] * g->mu[1] + g->Rc[6 + k] * g->mu[2];
 
   const int gs_div = (int)cfg[CFG_DIV] == 1;
-  if ((int)cam[CAM_MIP]) {
+  if ((int)cam[CAM_MIP] == 1) {
     /* Eq. mip with the pixel-invariant Sigma^ = Sigma + lambda I */
     double mu2 = g->mu[0] * g->mu[0] + g->mu[1] * g->mu[1] + g->mu[2] * g->mu[2];
     double lam = cfg[CFG_MIPS2] * mu2 / (cam[CAM_FX] * cam[CAM_FY]);
@@ -489,6 +496,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
   const double fx = cam[CAM_FX], fy = cam[CAM_FY], cx = cam[CAM_CX], cy = cam[CAM_CY];
   const double pmin = cfg[CFG_PMIN], tstop = cfg[CFG_TSTOP], amax = cfg[CFG_AMAX];
   const int gs_div = (int)cfg[CFG_DIV] == 1;
+  const int mip_exact = (int)cam[CAM_MIP] == 2;
+  const double sig2 = cfg[CFG_MIPS2] / (fx * fy); /* sigma^2 per unit distance on the axis */
 
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t p = 0; p < n_pix; ++p) {
@@ -500,8 +509,44 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
     uint64_t h = 1469598103934665603ull;
     for (int64_t k = 0; k < nv; ++k) {
       const prim *g = order[k];
-      double D;
-      if (gs_div) {
+      double D, mod = 1.0;
+      if (mip_exact) {
+        /* Sec. 5: unit ray xh, tau(xh) under Sigma, lambda = sigma_x^2 tau^2, then D_ray and
+         * the modulation under Sigma^_x = Sigma + lambda I, both in Sigma's eigenframe
+         * (Sigma = R_c diag(s^2) R_c^T, so Sigma^_x = R_c diag(s^2 + lambda) R_c^T). */
+        const double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        const double xh[3] = {x[0] / xn, x[1] / xn, x[2] / xn};
+        double a[3], b[3]; /* R_c^T xh and R_c^T mu */
+        for (int j = 0; j < 3; ++j) {
+          a[j] = g->Rc[j] * xh[0] + g->Rc[3 + j] * xh[1] + g->Rc[6 + j] * xh[2];
+          b[j] = g->Rc[j] * g->mu[0] + g->Rc[3 + j] * g->mu[1] + g->Rc[6 + j] * g->mu[2];
+        }
+        double n0 = 0, d0 = 0;
+        for (int j = 0; j < 3; ++j) {
+          const double s2 = g->s[j] * g->s[j];
+          n0 += b[j] * a[j] / s2;
+          d0 += a[j] * a[j] / s2;
+        }
+        const double tau = n0 / d0;
+        if (!(tau > 0)) continue;
+        const double cth = 1.0 / xn; /* cos of the ray's angle to the optical axis */
+        const double lam = sig2 * cth * cth * cth * tau * tau;
+        double n1 = 0, d1 = 0, ratio = 1;
+        for (int j = 0; j < 3; ++j) {
+          const double s2 = g->s[j] * g->s[j], sh2 = s2 + lam;
+          n1 += b[j] * a[j] / sh2;
+          d1 += a[j] * a[j] / sh2;
+          ratio *= s2 / sh2;
+        }
+        const double tauh = n1 / d1;
+        if (!(tauh > 0)) continue;
+        D = 0; /* (tauh xh - mu)^T Sigma^_x^-1 (tauh xh - mu) */
+        for (int j = 0; j < 3; ++j) {
+          const double r = tauh * a[j] - b[j];
+          D += r * r / (g->s[j] * g->s[j] + lam);
+        }
+        mod = sqrt(ratio * d0 / d1);
+      } else if (gs_div) {
         /* Sec. 3.1: (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), pi(x) the pixel centre */
         const double dx = (px + 0.5) - g->u[0], dy = (py + 0.5) - g->u[1];
         D = g->A[0] * dx * dx + 2.0 * g->A[1] * dx * dy + g->A[2] * dy * dy;
@@ -515,9 +560,9 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
         double r0 = tau * w[0] - g->m[0], r1 = tau * w[1] - g->m[1], r2 = tau * w[2] - g->m[2];
         D = r0 * r0 + r1 * r1 + r2 * r2;
       }
-      double om = g->o * exp(-0.5 * D);
+      double om = g->o * mod * exp(-0.5 * D);
       if (fabs(om - pmin) <= 1e-6) fl |= FLAG_CUTOFF;
-      if (!(D <= g->kappa)) continue;
+      if (mip_exact ? !(om >= pmin) : !(D <= g->kappa)) continue;
       if (om > amax) om = amax;
       double Tn = T * (1.0 - om);
       if (fabs(Tn - tstop) <= 1e-4 * tstop) fl |= FLAG_STOP;

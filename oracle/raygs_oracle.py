@@ -68,6 +68,17 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def mip_mode(m) -> int:
+    """Camera anti-aliasing mode: 0 off, 1 (or True) the pixel-invariant Eq. mip, 2 (or
+    "exact") the pixel-dependent form of Sec. 5."""
+    if m == "exact":
+        return 2
+    m = int(m)
+    if m not in (0, 1, 2):
+        raise ValueError(f"mip mode {m}")
+    return m
+
+
 def cam_array(cam: dict) -> np.ndarray:
     """Camera dict (scenes.make_camera) -> 20 doubles holding its float32 values."""
     a = np.zeros(20, dtype=np.float64)
@@ -77,7 +88,7 @@ def cam_array(cam: dict) -> np.ndarray:
     a[6:15] = np.asarray(cam["R"], dtype=np.float32).reshape(9)
     a[15:18] = np.asarray(cam["t"], dtype=np.float32).reshape(3)
     a[18] = np.float32(cam.get("near", 0.01))
-    a[19] = 1.0 if cam.get("mip", False) else 0.0
+    a[19] = float(mip_mode(cam.get("mip", False)))
     return a
 
 

@@ -148,7 +148,8 @@ def make_cameras(cams) -> C.Array:
         for k in range(3):
             a.t[k] = float(t[k])
         a.near_z = float(c.get("near", 0.01))
-        a.mip = 1 if c.get("mip", False) else 0
+        m = c.get("mip", False)
+        a.mip = 2 if m == "exact" else int(m)
     return arr
 
 

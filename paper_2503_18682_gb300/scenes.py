@@ -40,7 +40,8 @@ def _unit_quats(rng: np.random.Generator, n: int) -> np.ndarray:
 
 def make_camera(width, height, fx, fy, cx=None, cy=None, R=None, t=None,
                 near=0.01, mip=False) -> dict:
-    """A pinhole camera record (all floating fields float32 values)."""
+    """A pinhole camera record (all floating fields float32 values).  mip: False / 0 none,
+    True / 1 the pixel-invariant anti-aliasing term, "exact" / 2 the pixel-dependent one."""
     if cx is None:
         cx = width / 2.0
     if cy is None:
@@ -49,7 +50,7 @@ def make_camera(width, height, fx, fy, cx=None, cy=None, R=None, t=None,
     t = np.zeros(3, dtype=F32) if t is None else np.asarray(t, dtype=F32)
     return dict(width=int(width), height=int(height), fx=F32(fx), fy=F32(fy),
                 cx=F32(cx), cy=F32(cy), R=R.reshape(3, 3), t=t.reshape(3),
-                near=F32(near), mip=bool(mip))
+                near=F32(near), mip=(2 if mip == "exact" else int(mip)))
 
 
 def look_at(eye, target, up=(0.0, 1.0, 0.0)):

@@ -586,3 +586,106 @@ def test_gs_refuses_mip_and_skips_no_inside_camera(oracle_lib):
     assert np.any(oracle_lib.render(sc, cam, cfg=dict(divergence=1))["ncontrib"] > 0)
     with pytest.raises(RuntimeError):
         oracle_lib.render(sc, dict(cam, mip=True), cfg=dict(divergence=1))
+
+
+# ---------------------------------------------------------------- exact pixel-dependent MIP (Sec. 5)
+
+def _single_T(om):
+    return np.where(om >= PMIN, 1.0 - np.minimum(om, 0.99), 1.0)
+
+
+def test_mip_exact_isotropic_closed_form(oracle_lib):
+    """Sigma = s^2 I seen off-axis through a wide field of view.  By hand, for the unit ray
+    xh: tau = mu . xh, lambda = sigma^2 cos^3(theta) tau^2 / (fx fy) with cos(theta) = 1/|x|,
+    Sigma^_x = (s^2 + lambda) I, so D = |mu x xh|^2 / (s^2 + lambda) and the modulation is
+    sqrt(s^6 s^-2 / ((s^2 + lambda)^3 (s^2 + lambda)^-1)) = s^2 / (s^2 + lambda)."""
+    mu = np.array([0.3, -0.2, 2.0])
+    s, logit, sig2 = 0.3, 1.0, 10.0
+    sc = single(mu, np.log([s] * 3), [1, 0, 0, 0], logit, [1, 1, 1])
+    cam = scenes.make_camera(48, 40, 22.0, 19.0, 24.0, 20.0, mip="exact")
+    out = oracle_lib.render(sc, cam, cfg=dict(mip_sigma2=sig2))
+    j, i = np.divmod(np.arange(48 * 40), 48)
+    x = np.stack([(i + 0.5 - 24.0) / 22.0, (j + 0.5 - 20.0) / 19.0, np.ones(i.size)], axis=1)
+    xn = np.linalg.norm(x, axis=1)
+    xh = x / xn[:, None]
+    muf = np.float32(mu).astype(np.float64)
+    sf = math.exp(float(np.float32(np.log(s))))
+    tau = xh @ muf
+    lam = sig2 * xn ** -3 * tau ** 2 / (22.0 * 19.0)
+    D = np.sum(np.cross(muf, xh) ** 2, axis=1) / (sf ** 2 + lam)
+    o = 1.0 / (1.0 + math.exp(-float(np.float32(logit))))
+    om = o * sf ** 2 / (sf ** 2 + lam) * np.exp(-D / 2)
+    np.testing.assert_allclose(out["T"], _single_T(om), rtol=1e-12, atol=1e-14)
+    assert np.count_nonzero(out["ncontrib"]) > 100
+    assert (lam / sf ** 2).max() > 0.5  # the smoothing is not negligible here
+
+
+def test_mip_exact_tangent_plane_restatement(oracle_lib):
+    """The appendix's tangent-plane form, restated independently: an orthonormal F with
+    F^T xh = 0 (numpy null space), A = F^T Sigma F, A^ = A + lambda I, D = (F^T mu)^T A^-1
+    (F^T mu), modulation sqrt(det A / det A^), Sigma from scipy's rotation, tau from
+    np.linalg.inv(Sigma).  It equals the oracle's eigenframe evaluation of D_ray(x; mu,
+    Sigma^_x) and sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x))."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(31)
+    cam = scenes.make_camera(40, 36, 30.0, 26.0, 19.5, 18.0, mip="exact")
+    sig2 = 25.0
+    checked = 0
+    for _ in range(10):
+        mu = np.float32(np.array([*rng.uniform(-0.3, 0.3, 2), rng.uniform(1.5, 3.0)]))
+        ls = np.float32(np.log(rng.uniform(0.02, 0.2, 3)))
+        q = np.float32(rand_rot(rng))
+        sc = single(mu, ls, q, 1.5, [1, 1, 1])
+        out = oracle_lib.render(sc, cam, cfg=dict(mip_sigma2=sig2))
+        Rq = Rot.from_quat(q.astype(np.float64)[[1, 2, 3, 0]]).as_matrix()
+        S = Rq @ np.diag(np.exp(2 * ls.astype(np.float64))) @ Rq.T
+        Si = np.linalg.inv(S)
+        m = mu.astype(np.float64)
+        o = 1.0 / (1.0 + math.exp(-float(np.float32(1.5))))
+        T = np.ones(40 * 36)
+        for p in range(40 * 36):
+            jj, ii = divmod(p, 40)
+            x = np.array([(ii + 0.5 - 19.5) / 30.0, (jj + 0.5 - 18.0) / 26.0, 1.0])
+            xh = x / np.linalg.norm(x)
+            tau = (m @ Si @ xh) / (xh @ Si @ xh)
+            if tau <= 0:
+                continue
+            lam = sig2 * (1.0 / np.linalg.norm(x)) ** 3 * tau ** 2 / (30.0 * 26.0)
+            Sh = S + lam * np.eye(3)
+            Shi = np.linalg.inv(Sh)
+            if (m @ Shi @ xh) <= 0:
+                continue
+            F = np.linalg.svd(xh[None, :])[2][1:].T          # 3x2, orthonormal, F^T xh = 0
+            A = F.T @ S @ F
+            Ah = A + lam * np.eye(2)
+            pp = F.T @ m
+            D = pp @ np.linalg.solve(Ah, pp)
+            om = o * math.sqrt(np.linalg.det(A) / np.linalg.det(Ah)) * math.exp(-D / 2)
+            if abs(om - PMIN) < 1e-9:
+                continue
+            T[p] = _single_T(np.array(om))
+        np.testing.assert_allclose(out["T"], T, rtol=1e-9, atol=1e-12)
+        checked += np.count_nonzero(out["ncontrib"])
+    assert checked > 500
+
+
+def test_mip_exact_limits(oracle_lib):
+    """sigma -> 0 gives the plain image; on the optical axis, at the pixel whose ray passes
+    through the mean, the exact form equals the pixel-invariant Eq. mip (tau = |mu|,
+    cos(theta) = 1, x ∝ mu so x^T Sigma^-1 x / x^T Sigma^^-1 x = c^2 / c^^2 and D = 0)."""
+    sc, cams = scenes.workload_small()
+    cam = dict(cams[0])
+    plain = oracle_lib.render(sc, cam)
+    zero = oracle_lib.render(sc, dict(cam, mip="exact"), cfg=dict(mip_sigma2=0.0))
+    np.testing.assert_allclose(zero["rgb"], plain["rgb"], rtol=1e-10, atol=1e-13)
+    np.testing.assert_array_equal(zero["ncontrib"], plain["ncontrib"])
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        one = single([0.0, 0.0, rng.uniform(2, 4)], np.log(rng.uniform(0.002, 0.02, 3)), rand_rot(rng), 0.8,
+                     [1, 1, 1])
+        c1 = scenes.make_camera(1, 1, 64.0, 64.0, 0.5, 0.5)
+        ex = oracle_lib.render(one, dict(c1, mip="exact"), cfg=dict(mip_sigma2=2.0))
+        ap = oracle_lib.render(one, dict(c1, mip=True), cfg=dict(mip_sigma2=2.0))
+        pl = oracle_lib.render(one, c1)
+        assert ex["T"][0] == pytest.approx(ap["T"][0], rel=1e-12)
+        assert ex["T"][0] > pl["T"][0]  # the smoothing lowers the peak opacity
