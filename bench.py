@@ -488,11 +488,12 @@ def divergence_ab_720p(cfg, dev):
 
 
 def antialiasing(args, dev):
-    """The 720p MIP workload (500k primitives, 1280x720) three ways: one ray per pixel
-    without the MIP term, with the paper's MIP term (Eq. mip), and 2x2 supersampled without
-    it (four sub-pixel rays, box-filter resolve; the counterpart of the paper's MSAA
-    comparison).  Forward time of each, and the first two images against the supersampled
-    one (max-abs, PSNR)."""
+    """The 720p MIP workload (500k primitives, 1280x720) four ways: one ray per pixel
+    without the MIP term, with the paper's pixel-invariant MIP term (Eq. mip), with the
+    exact pixel-dependent form it approximates (Sec. 5), and 2x2 supersampled without any
+    (four sub-pixel rays, box-filter resolve; the counterpart of the paper's MSAA
+    comparison).  Forward time of each, each image against the supersampled one, and the
+    error of the approximation (Eq. mip against the exact form) (max-abs, PSNR)."""
     import torch
     from paper_2503_18682_gb300 import raygs, scenes
     scene, cams_mip = scenes.workload_mip_720p()
@@ -525,6 +526,7 @@ def antialiasing(args, dev):
 
     _, img_plain, ms_plain = timed_forward(plain)
     _, img_mip, ms_mip = timed_forward(cams_mip)
+    _, img_mipx, ms_mipx = timed_forward([dict(c, mip="exact") for c in cams_mip])
     r_ss, img_hi, ms_ss = timed_forward(raygs.supersampled_cameras(plain, 2))
     img_ss = torch.empty_like(img_plain)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -533,13 +535,15 @@ def antialiasing(args, dev):
     e1.record()
     e1.synchronize()
 
-    def err(a):
-        mse = float(((a - img_ss).double() ** 2).mean())
-        return dict(max_abs=float((a - img_ss).abs().max()), psnr_db=(99.0 if mse == 0 else -10 * np.log10(mse)))
+    def err(a, ref=None):
+        ref = img_ss if ref is None else ref
+        mse = float(((a - ref).double() ** 2).mean())
+        return dict(max_abs=float((a - ref).abs().max()), psnr_db=(99.0 if mse == 0 else -10 * np.log10(mse)))
 
     return dict(workload=f"{n} blob primitives, 1280x720", one_ray_ms=ms_plain, mip_ms=ms_mip,
-                supersampled_2x2_ms=ms_ss + e0.elapsed_time(e1),
-                one_ray_vs_supersampled=err(img_plain), mip_vs_supersampled=err(img_mip))
+                mip_exact_ms=ms_mipx, supersampled_2x2_ms=ms_ss + e0.elapsed_time(e1),
+                one_ray_vs_supersampled=err(img_plain), mip_vs_supersampled=err(img_mip),
+                mip_exact_vs_supersampled=err(img_mipx), mip_vs_mip_exact=err(img_mip, img_mipx))
 
 
 def precision_storage(args, dev):

@@ -67,14 +67,27 @@ typedef struct {
   int32_t sh_dtype;           /* raygs_dtype: F32, F16 or BF16 */
 } raygs_scene;
 
-/* One pinhole view (Sec. 3.1).  mip != 0 applies the anti-aliasing filter of Sec. 5. */
+/* Anti-aliasing of a view (Sec. 5).
+ *   RAYGS_MIP_OFF:    none.
+ *   RAYGS_MIP_APPROX: Eq. mip, the pixel-invariant Sigma^ = Sigma + lambda I with
+ *                     lambda = mip_sigma2 |mu|^2 / (fx fy) and the opacity modulated by
+ *                     sqrt(|Sigma| c^2 / (|Sigma^| c^^2)).
+ *   RAYGS_MIP_EXACT:  the pixel-dependent form that Eq. mip approximates: per pixel ray x,
+ *                     Sigma^_x = Sigma + sigma_x^2 tau(x)^2 I with sigma_x^2 = mip_sigma2
+ *                     cos^3(theta_x) / (fx fy) and tau(x) the ray's maximum-density depth;
+ *                     omega = o m(x) exp(-D_ray(x; mu, Sigma^_x) / 2) with
+ *                     m(x) = sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x)).
+ *                     A plan's views are either all EXACT or none; no backward. */
+typedef enum { RAYGS_MIP_OFF = 0, RAYGS_MIP_APPROX = 1, RAYGS_MIP_EXACT = 2 } raygs_mip;
+
+/* One pinhole view (Sec. 3.1). */
 typedef struct {
   float fx, fy, cx, cy;
   int32_t width, height; /* 1 .. 32768 each */
   float R[9];            /* world -> camera rotation, row-major */
   float t[3];
   float near_z;          /* primitives whose centre depth is <= near_z are culled (Sec. 4.1) */
-  int32_t mip;
+  int32_t mip;           /* raygs_mip */
 } raygs_camera;
 
 /* The divergence D that weighs a primitive at a pixel, omega = o exp(-D/2).
@@ -282,7 +295,8 @@ size_t raygs_autotune_workspace_bytes(const raygs_camera *cams, int32_t n_views,
  * deployment variant of the hot path.
  *
  *  - Inputs/outputs as in raygs_preprocess and raygs_render (caller-owned device buffers);
- *    cams is a host array of n_views cameras; cfg may be NULL for the defaults.
+ *    cams is a host array of n_views cameras; cfg may be NULL for the defaults.  Views with
+ *    RAYGS_MIP_EXACT are refused (INVALID_ARG).
  *  - Size limit: the per-(primitive, view) buffers (about 140 bytes each), the tile ranges
  *    and a sort histogram must fit in the array, and the remaining space bounds the
  *    (primitive, tile) instances.  A problem that does not fit is rejected with

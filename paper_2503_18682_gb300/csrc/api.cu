@@ -96,7 +96,8 @@ raygs_status raygs_plan_create(const raygs_camera *cams, int32_t n_views, int64_
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  w.L = make_layout(n_views, n_gaussians, tb, trows, max_instances, w.G, max_tx, cfg.enable_backward != 0);
+  w.L = make_layout(n_views, n_gaussians, tb, trows, max_instances, w.G, max_tx, cfg.enable_backward != 0,
+                    cams[0].mip == RAYGS_MIP_EXACT);
   p->total_pixels = pb;
   *out = p;
   return RAYGS_OK;

@@ -602,7 +602,9 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
         const DevCam &cam = R.cams[pair / uint32_t(R.n)];
         const float ya = float(ty * R.tile_h) + 0.5f;
         const float yb = float(min((ty + 1) * uint32_t(R.tile_h), uint32_t(cam.H))) - 0.5f;
-        if (!(el.a > 0.f)) {
+        if (el.a == -2.f) {
+          // the whole rectangle row (a bound without a conic of its own)
+        } else if (!(el.a > 0.f)) {
           const Rec rc = R.rec[pair];
           int a0, b0;
           if (!support_tile_span(rc, cam, R.tile_w, ya, yb, int(tx0), int(tx1), a0, b0)) {

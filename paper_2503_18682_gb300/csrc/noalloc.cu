@@ -68,6 +68,7 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   int64_t tiles = 0, trows = 0, pixels = 0;
   int max_tx = 0;
   if (!plan_views(cams, n_views, cfg, dc, tiles, trows, pixels, max_tx)) return RAYGS_ERR_INVALID_ARG;
+  if (cams[0].mip == RAYGS_MIP_EXACT) return RAYGS_ERR_INVALID_ARG;  // needs the second record buffer
 
   void *scratch = nullptr;
   s = scratch_for_current_device(&scratch);
@@ -87,13 +88,13 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   w.num_sms = sms;
   w.G = sort_grid(sms);
   w.cfg = cfg;
-  const Layout L0 = make_layout(n_views, n, tiles, trows, 0, w.G, max_tx, false);
+  const Layout L0 = make_layout(n_views, n, tiles, trows, 0, w.G, max_tx, false, false);
   if (L0.total + 8192 > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   int64_t cap = int64_t((kNoAllocScratchBytes - L0.total - 8192) / (kBytesPerCapacity + 1));
-  w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false);
+  w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false, false);
   while (w.L.total > kNoAllocScratchBytes && cap > 0) {
     cap -= 4096;
-    w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false);
+    w.L = make_layout(n_views, n, tiles, trows, cap, w.G, max_tx, false, false);
   }
   if (cap <= 0 || w.L.total > kNoAllocScratchBytes) return RAYGS_ERR_CAPACITY;
   w.cap = cap;

@@ -19,7 +19,7 @@ void fill_devcam(const raygs_camera &c, const raygs_config &cfg, DevCam &d) {
   for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
   for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
   d.near_z = c.near_z;
-  d.mip = c.mip ? 1 : 0;
+  d.mip = c.mip;
   for (int k = 0; k < 3; ++k)
     d.C[k] = float(-(double(c.R[k]) * c.t[0] + double(c.R[3 + k]) * c.t[1] + double(c.R[6 + k]) * c.t[2]));
   d.xmin = float((0.5 - double(c.cx)) / double(c.fx));
@@ -45,7 +45,7 @@ bool config_valid(const raygs_config &cfg) {
 bool camera_valid(const raygs_camera &c) {
   return c.width >= 1 && c.height >= 1 && c.width <= 32768 && c.height <= 32768 && c.fx > 0.f && c.fy > 0.f &&
          std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy) &&
-         c.near_z > 0.f;
+         c.near_z > 0.f && c.mip >= RAYGS_MIP_OFF && c.mip <= RAYGS_MIP_EXACT;
 }
 
 raygs_status scene_valid(const raygs_scene *s, int64_t n) {
@@ -77,7 +77,7 @@ int tile_sort_bits(int64_t tiles) {
 }
 
 Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, int max_tiles_x,
-                   bool backward) {
+                   bool backward, bool mip_exact) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = up256(o + bytes); return r; };
@@ -91,6 +91,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.rect = take(8 * VN);
   L.ell = take(sizeof(Ell) * VN);
   L.rec = take(sizeof(Rec) * VN);
+  L.recx = mip_exact ? take(sizeof(Rec) * VN) : 0;
   for (int i = 0; i < 2; ++i) { L.s1k[i] = take(4 * VN); L.s1v[i] = take(4 * VN); }
   L.off = take(4 * VN);
   L.partial = take(4 * size_t(G));
@@ -124,6 +125,8 @@ bool plan_views(const raygs_camera *cams, int n_views, const raygs_config &cfg, 
   for (int v = 0; v < n_views; ++v) {
     if (!camera_valid(cams[v])) return false;
     if (cfg.divergence == 1 && cams[v].mip) return false;  // Eq. mip is a RayGS term
+    // the exact anti-aliasing uses its own record and rasteriser for the whole batch
+    if ((cams[v].mip == RAYGS_MIP_EXACT) != (cams[0].mip == RAYGS_MIP_EXACT)) return false;
     fill_devcam(cams[v], cfg, dc[v]);
     if (dc[v].tiles_x > kMaxTilesX) return false;
     dc[v].tile_base = int(tiles);
@@ -165,6 +168,7 @@ cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st) {
   P.rect = w.at<uint2>(w.L.rect);
   P.ell = w.at<Ell>(w.L.ell);
   P.rec = w.at<Rec>(w.L.rec);
+  P.recx = w.L.recx ? w.at<Rec>(w.L.recx) : nullptr;
   P.counters = w.at<Counters>(w.L.counters);
   P.deg_list = w.at<uint32_t>(w.L.deg);
   P.deg_count = w.at<uint32_t>(w.L.degc);
@@ -313,6 +317,8 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
   P.t_stop = w.cfg.t_stop;
   P.alpha_max = w.cfg.alpha_max;
   P.qmix = w.cfg.divergence == 1 ? 0.f : 1.f;
+  P.recx = w.L.recx ? w.at<Rec>(w.L.recx) : nullptr;
+  P.p_min = w.cfg.p_min;
   P.rgb = rgb;
   P.Tf = T_final;
   P.ncontrib = n_contrib;
@@ -321,6 +327,7 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
     cudaError_t e = cudaMemsetAsync(P.eval_counts, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
+  if (P.recx) return launch_render_mipx(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);
   return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.cfg.batch_records, w.tiles, count, st);
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ bool tile_rect(bool full, float xmn, float xmx, float
 // covers no pixel of this view.
 template <typename T>
 __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, const DevCam &cam,
-                           float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out) {
+                           float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out,
+                           bool apply_mip = true) {
   // R_c = R_wc R_p: columns n_k are the primitive's axes in the camera frame.
   T Rc[9];
 #pragma unroll
@@ -84,7 +85,7 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
     pk[k] = Rc[k] * mu[0] + Rc[3 + k] * mu[1] + Rc[6 + k] * mu[2];  // n_k . mu
     s[k] = s_in[k];
   }
-  if (cam.mip) {
+  if (apply_mip && cam.mip == RAYGS_MIP_APPROX) {
     // Sec. 5, Eq. mip: Sigma^ = Sigma + lam I with lam = sigma^2 |mu|^2 / (fx fy); the
     // opacity is modulated by sqrt(|Sigma| c^2 / (|Sigma^| c^^2)).
     T lam = T(mip_sigma2) * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) /
@@ -305,6 +306,125 @@ __device__ bool gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, c
                    tile_h, out);
 }
 
+// Per-pixel constants of the exact anti-aliasing (Sec. 5, pixel-dependent form), in the
+// frame of Sigma's axes (camera-frame columns r_k of R_c, scales s_k), for the pixel offset
+// delta = p - u from the projected centre and the ray x = (X, Y, 1):
+//   y_k = (r_k . x) / s_k = b_k + g_k . delta                  whitened ray (S^-1 R_c^T x)
+//   e_k = (m x y)_k = (s_k / s0 s1 s2) r_k . (mu x (x - mu / mu_z)) = A_k . delta
+//                                                              (m = S^-1 R_c^T mu), exact
+//                                                              in delta, no cancellation
+//   tau = m . y / |y|^2 (Sigma), lambda = sigma^2 cos^3(theta) tau_unit^2 / (fx fy)
+//       = (sigma^2 / (fx fy)) tau^2 / |x|,   u_k = 1 + lambda / s_k^2 = 1 + (tau^2 / |x|) w_k
+// and with Sigma^_x = Sigma + lambda I (Lagrange's identity in the weighted frame)
+//   D_ray(x; mu, Sigma^_x) = sum_k u_k e_k^2 / sum_k y_k^2 prod_{j != k} u_j = Num / Den
+//   m(x)^2 = |Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x) = |y|^2 / Den
+//   tau^_x > 0  <=>  sum_k m_k y_k prod_{j != k} u_j > 0.
+struct MipxOut {
+  float A[6], g[6], b[3], m[3], w[3], kappa;
+};
+
+// The exact anti-aliasing stage.  The binning support is that of the primitive inflated to
+// Sigma + Lambda I, Lambda a bound of lambda(x) over the rays the primitive reaches: there
+// D^ <= kappa (the modulation is <= 1), so the Sigma^-closest point lies within
+// sqrt(kappa (s_max^2 + lambda)) of mu, tau differs from its depth by at most
+// s_max sqrt(kappa (1 + lambda / s_min^2)), hence tau <= (|mu| + 2 sqrt(kappa) s_max) / (1 - k)
+// with k = sqrt(kappa) sigma_a (1 + s_max / s_min) < 1 (sigma_a^2 = sigma^2 / (fx fy) bounds
+// sigma_x^2), and D^(x) >= D(x; Sigma + Lambda I) for lambda(x) <= Lambda.  When k >= 1/2, or
+// when the inflated support reaches the camera, the pair covers its whole view.
+template <typename T>
+__device__ bool mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
+                                float mip_sigma2, int tile_w, int tile_h, StageOut &out, MipxOut &X) {
+  const T kappa = T(2) * t_log(o / T(p_min));
+  if (!(kappa > T(0))) return false;
+  T Rc[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Rc[3 * i + j] = T(cam.R[3 * i]) * Rp[j] + T(cam.R[3 * i + 1]) * Rp[3 + j] +
+                      T(cam.R[3 * i + 2]) * Rp[6 + j];
+  T pk[3], mt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    pk[k] = Rc[k] * mu[0] + Rc[3 + k] * mu[1] + Rc[6 + k] * mu[2];
+    mt[k] = pk[k] / s[k];
+  }
+  const T c2 = mt[0] * mt[0] + mt[1] * mt[1] + mt[2] * mt[2];
+  if (!(c2 > kappa)) return false;  // Eq. c on the plain primitive
+  const T smax = fmax(fmax(s[0], s[1]), s[2]), smin = fmin(fmin(s[0], s[1]), s[2]);
+  const T sa2 = T(mip_sigma2) / (T(cam.fx) * T(cam.fy));
+  const T kk = t_sqrt(kappa) * t_sqrt(sa2) * (T(1) + smax / smin);
+  bool full = true;
+  out.illcond = true;
+  if (kk < T(0.5)) {
+    const T mun = t_sqrt(mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]);
+    const T taumax = (mun + T(2) * t_sqrt(kappa) * smax) / (T(1) - kk);
+    const T Lam = sa2 * taumax * taumax * T(1.001);
+    T sI[3], c2I = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sI[k] = t_sqrt(s[k] * s[k] + Lam);
+      c2I += pk[k] * pk[k] / (sI[k] * sI[k]);
+    }
+    if (c2I > kappa * T(1.001)) {
+      full = false;
+      if (!view_stage<T>(mu, Rp, sI, o, cam, p_min, 0.f, tile_w, tile_h, out, false)) return false;
+      if (!(out.M00 > 0.f)) out.M00 = -2.f;  // not a bounded ellipse: whole rectangle rows
+    }
+  }
+  if (full) {
+    out.tx0 = 0; out.ty0 = 0;
+    out.tx1 = (cam.W - 1) / tile_w; out.ty1 = (cam.H - 1) / tile_h;
+    out.M00 = -2.f; out.M01 = 0.f; out.M11 = 0.f; out.det = 0.f; out.dc0 = 0.f; out.dc1 = 0.f;
+  }
+  const T ps = s[0] * s[1] * s[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T rx = Rc[k], ry = Rc[3 + k], rz = Rc[6 + k];
+    const T ck = s[k] / ps;
+    X.A[2 * k] = float(ck * (ry * mu[2] - rz * mu[1]) * T(cam.ifx));
+    X.A[2 * k + 1] = float(ck * (rz * mu[0] - rx * mu[2]) * T(cam.ify));
+    X.g[2 * k] = float(rx * T(cam.ifx) / s[k]);
+    X.g[2 * k + 1] = float(ry * T(cam.ify) / s[k]);
+    X.b[k] = float(mt[k] / mu[2]);
+    X.m[k] = float(mt[k]);
+    X.w[k] = float(sa2 / (s[k] * s[k]));
+  }
+  X.kappa = float(kappa);
+  out.lo2o = float(t_log(o) * T(1.4426950408889634));
+  return true;
+}
+
+__device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t idx, const DevCam &cam,
+                                                  const df muc[3], const StageOut &so, const MipxOut &X,
+                                                  const float rgb[3], float z) {
+  df Xc = df_div(muc[0], muc[2]);
+  df Yc = df_div(muc[1], muc[2]);
+  df u = df_add(df_mul_f(Xc, cam.fx), df{cam.cx, 0.f});
+  df v = df_add(df_mul_f(Yc, cam.fy), df{cam.cy, 0.f});
+  Rec r, q;
+  r.a = make_float4(u.hi, v.hi, u.lo, v.lo);
+  r.b = make_float4(X.A[0], X.A[1], X.A[2], X.A[3]);
+  r.c = make_float4(X.A[4], X.A[5], X.g[0], X.g[1]);
+  r.d = make_float4(X.g[2], X.g[3], X.g[4], X.g[5]);
+  q.a = make_float4(X.b[0], X.b[1], X.b[2], so.lo2o);
+  q.b = make_float4(X.m[0], X.m[1], X.m[2], X.kappa);
+  q.c = make_float4(X.w[0], X.w[1], X.w[2], 0.f);
+  q.d = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+  P.rec[idx] = r;
+  P.recx[idx] = q;
+  P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
+                           uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
+  Ell e;
+  e.r0 = uint32_t(so.tx0) | (uint32_t(so.ty0) << 16);
+  e.r1 = uint32_t(so.tx1) | (uint32_t(so.ty1) << 16);
+  e.cx = u.hi + so.dc0;
+  e.cy = v.hi + so.dc1;
+  e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
+  P.ell[idx] = e;
+  P.depth_key[idx] = __float_as_uint(z);
+}
+
 __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, const DevCam &cam,
                                              const df muc[3], const StageOut &so, const float rgb[3],
                                              float z) {
@@ -337,7 +457,21 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
 // pair for the full stage, whose own tests decide.
 constexpr int kViewChunk = 16;
 
-template <int DEG>
+// Stage variants, one per plan (compiled apart so that the RayGS stage keeps its registers):
+// RayGS with or without Eq. mip per view, the GS divergence, and RayGS with the exact
+// pixel-dependent anti-aliasing in every view.
+enum StageMode { kStageRay = 0, kStageGS = 1, kStageExact = 2 };
+
+template <int MODE, typename T>
+__device__ __forceinline__ bool stage_for(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam,
+                                          const PrepParams &P, StageOut &so, MipxOut &mx) {
+  if (MODE == kStageGS) return gs_view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.tile_w, P.tile_h, so);
+  if (MODE == kStageExact)
+    return mipx_view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so, mx);
+  return view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so);
+}
+
+template <int DEG, int MODE>
 __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) {
   constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
   constexpr int SHP = K3 + 1;  // padded row
@@ -430,7 +564,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
             const float rad = sk * sqrtf(s2) * 1.01f + 1e-5f * (fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2])) + 1e-5f;
             // the GS support is the linearised projection, not bounded by the sphere's
             // cone: its exact screen box decides in the full stage
-            keep = P.divergence == 1 || !outside_frustum<float>(mu, rad, cam);
+            keep = MODE != kStageRay || !outside_frustum<float>(mu, rad, cam);
           }
         }
         if (!keep) P.depth_key[idx] = kCulled;
@@ -460,10 +594,8 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
 #pragma unroll
       for (int k = 0; k < 9; ++k) Rp[k] = s_R[9 * tt + k];
       StageOut so;
-      const bool vis = P.divergence == 1
-                           ? gs_view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.tile_w, P.tile_h, so)
-                           : view_stage<float>(mu, Rp, sv, s_o[tt], cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so);
-      if (!vis) {
+      MipxOut mxo;
+      if (!stage_for<MODE, float>(mu, Rp, sv, s_o[tt], cam, P, so, mxo)) {
         P.depth_key[idx] = kCulled;
         continue;
       }
@@ -471,7 +603,8 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
       float rgb[3];
       sh_colour<DEG>(s_sh + tt * SHP, dx * dn, dy * dn, dz * dn, rgb);
-      write_record(P, idx, cam, muc, so, rgb, z);
+      if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z);
+      else write_record(P, idx, cam, muc, so, rgb, z);
       if (s_deg[tt] && (P.fp64_degenerate == 2 || so.illcond)) {
         const uint32_t slot = atomicAdd(P.deg_count, 1u);
         P.deg_list[slot] = uint32_t(idx);
@@ -484,7 +617,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
 // FP64 vertex stage for the (view, primitive) pairs listed by preprocess_kernel.  The
 // float32 record, rectangle and key of each pair are overwritten.  Grid-stride over the
 // device-side list.
-template <int DEG>
+template <int DEG, int MODE>
 __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t count = *P.deg_count;
@@ -508,10 +641,8 @@ __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
     const double mu[3] = {double(muc[0].hi) + double(muc[0].lo), double(muc[1].hi) + double(muc[1].lo),
                           double(muc[2].hi) + double(muc[2].lo)};
     StageOut so;
-    const bool vis = P.divergence == 1 ? gs_view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.tile_w, P.tile_h, so)
-                                       : view_stage<double>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w,
-                                                            P.tile_h, so);
-    if (!vis) {
+    MipxOut mxo;
+    if (!stage_for<MODE, double>(mu, Rp, s, o, cam, P, so, mxo)) {
       P.depth_key[idx] = kCulled;
       continue;
     }
@@ -521,7 +652,8 @@ __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
     float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
     float rgb[3];
     sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
-    write_record(P, idx, cam, muc, so, rgb, z);
+    if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z);
+    else write_record(P, idx, cam, muc, so, rgb, z);
   }
 }
 
@@ -531,22 +663,37 @@ cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st)
   int blocks = (P.n + kPrepThreads - 1) / kPrepThreads;
   size_t dyn = sizeof(DevCam) * P.n_views;
   cudaMemsetAsync(P.deg_count, 0, sizeof(uint32_t), st);
+  const int mode = P.divergence == 1 ? kStageGS : P.recx ? kStageExact : kStageRay;
+#define RAYGS_PREP(D, M) preprocess_kernel<D, M><<<blocks, kPrepThreads, dyn, st>>>(P)
+#define RAYGS_PREP_MODES(D)                 \
+  if (mode == kStageGS) RAYGS_PREP(D, 1);         \
+  else if (mode == kStageExact) RAYGS_PREP(D, 2); \
+  else RAYGS_PREP(D, 0);
   switch (P.sh_degree) {
-    case 0: preprocess_kernel<0><<<blocks, kPrepThreads, dyn, st>>>(P); break;
-    case 1: preprocess_kernel<1><<<blocks, kPrepThreads, dyn, st>>>(P); break;
-    case 2: preprocess_kernel<2><<<blocks, kPrepThreads, dyn, st>>>(P); break;
-    default: preprocess_kernel<3><<<blocks, kPrepThreads, dyn, st>>>(P); break;
+    case 0: RAYGS_PREP_MODES(0) break;
+    case 1: RAYGS_PREP_MODES(1) break;
+    case 2: RAYGS_PREP_MODES(2) break;
+    default: RAYGS_PREP_MODES(3) break;
   }
+#undef RAYGS_PREP_MODES
+#undef RAYGS_PREP
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (P.fp64_degenerate) {
     int gb = num_sms * 4;
+#define RAYGS_FP64(D, M) preprocess_fp64_kernel<D, M><<<gb, 128, 0, st>>>(P)
+#define RAYGS_FP64_MODES(D)                 \
+  if (mode == kStageGS) RAYGS_FP64(D, 1);         \
+  else if (mode == kStageExact) RAYGS_FP64(D, 2); \
+  else RAYGS_FP64(D, 0);
     switch (P.sh_degree) {
-      case 0: preprocess_fp64_kernel<0><<<gb, 128, 0, st>>>(P); break;
-      case 1: preprocess_fp64_kernel<1><<<gb, 128, 0, st>>>(P); break;
-      case 2: preprocess_fp64_kernel<2><<<gb, 128, 0, st>>>(P); break;
-      default: preprocess_fp64_kernel<3><<<gb, 128, 0, st>>>(P); break;
+      case 0: RAYGS_FP64_MODES(0) break;
+      case 1: RAYGS_FP64_MODES(1) break;
+      case 2: RAYGS_FP64_MODES(2) break;
+      default: RAYGS_FP64_MODES(3) break;
     }
+#undef RAYGS_FP64_MODES
+#undef RAYGS_FP64
     e = cudaGetLastError();
   }
   return e;

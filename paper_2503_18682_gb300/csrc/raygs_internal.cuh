@@ -58,7 +58,9 @@ struct Counters {
 // its tile rectangle (as in the rect array) and the ellipse of pixel centres p with
 // (p - c)^T [[a, b], [b, d]] (p - c) <= 1 that holds exactly the rays with D <= kappa (up to
 // rounding), det = ad - b^2.  a < 0 marks a support that is not a bounded ellipse in the
-// image (or is too ill-conditioned in float32): binning then bounds it tile by tile.
+// image (or is too ill-conditioned in float32): binning then bounds it tile by tile from
+// the pair's record; a = -2 keeps every tile of the rectangle (the exact anti-aliasing
+// records hold no conic).
 struct __align__(32) Ell {
   uint32_t r0, r1;  // tx0 | ty0 << 16, tx1 | ty1 << 16
   float cx, cy, a, b, d, det;
@@ -161,6 +163,7 @@ struct PrepParams {
   uint2 *rect;
   Ell *ell;
   Rec *rec;
+  Rec *recx;            // second half of the exact anti-aliasing record (views with mip = 2)
   Counters *counters;
   uint32_t *deg_list;   // (view, primitive) pairs left to the FP64 kernel
   uint32_t *deg_count;
@@ -254,6 +257,8 @@ struct RenderParams {
   const Rec *rec;
   float t_stop, alpha_max;
   float qmix;  // 1: D_ray fragment formula, D ~ q / (q + r); 0: D_gs, D ~ q (records with h = 0)
+  const Rec *recx;  // exact anti-aliasing: second half of each record (then rec holds the first)
+  float p_min;
   float *rgb;
   float *Tf;
   int *ncontrib;
@@ -322,6 +327,8 @@ int expand_chunk_rows(int64_t cap, int max_tiles_x);
 int64_t expand_max_chunks(int64_t trows, int64_t cap, int chunk_rows);
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
                           bool count, cudaStream_t st);
+cudaError_t launch_render_mipx(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
+                               cudaStream_t st);
 cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, int64_t n_tiles, cudaStream_t st);
 cudaError_t launch_pair_grads(const PairGradParams &P, int G, cudaStream_t st);
 cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st);
@@ -331,13 +338,13 @@ cudaError_t launch_resolve(const float *rgb_hi, const float *T_hi, float *rgb_lo
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t cams, counters, evals, tscan, depth, rect, ell, rec, s1k[2], s1v[2], off, partial, rtstart,
+  size_t cams, counters, evals, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
       seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, cbase, ccnt, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };
 
 Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t cap, int G, int max_tiles_x,
-                   bool backward);
+                   bool backward, bool mip_exact);
 
 // Workspace bytes per unit of instance capacity (tile rows and instances share it).
 constexpr size_t kBytesPerCapacity = 8 + 4 + 4 + 2 * 4 + 2 * 8 + 4;
