@@ -72,7 +72,8 @@ __device__ __forceinline__ bool row_may_hit(const float4 &A, const float4 &B, co
 
 // Support test of PX pixels of one row (columns fl_x + k s, k = 0 .. PX-1, row fl_y,
 // relative to the tile origin; s a power of two).  Returns the hit mask; q, r (and y) per
-// pixel.
+// pixel.  With r = y2 |y2| the single test kp q - r <= 0 holds exactly when y2 > 0 and
+// kp q <= y2^2 (kp > 0, q >= 0; y = 0 cannot occur), and r = y2^2 on every hit.
 template <int PX>
 __device__ __forceinline__ uint32_t eval_pixels(const float4 &A, const float4 &B, float kp, float fl_x, float fl_y,
                                                 float s, float q[PX], float r[PX], float y0s[PX], float y1s[PX],
@@ -88,9 +89,9 @@ __device__ __forceinline__ uint32_t eval_pixels(const float4 &A, const float4 &B
   for (int k = 0; k < PX; ++k) {
     if (k) { y0 += st0; y1 += st1; y2 += st2; }
     q[k] = fmaf(y0, y0, y1 * y1);
-    r[k] = y2 * y2;
+    r[k] = y2 * fabsf(y2);
     y0s[k] = y0; y1s[k] = y1; y2s[k] = y2;
-    if (y2 > 0.f && fmaf(kp, q[k], -r[k]) <= 0.f) hit |= 1u << k;
+    if (fmaf(kp, q[k], -r[k]) <= 0.f) hit |= 1u << k;
   }
   return hit;
 }

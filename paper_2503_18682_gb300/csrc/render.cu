@@ -100,6 +100,9 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
       nxt[rr] = i < rg.y ? P.pairs[P.inst_vals[i]] : 0u;
     }
     const int nb = min(NB, int(rg.y - start));
+    // two records per iteration give the scheduler independent work (8 pixels per thread
+    // would spill)
+#pragma unroll(PX >= 8 ? 1 : 2)
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
       const float4 Cc = s_C[j];
