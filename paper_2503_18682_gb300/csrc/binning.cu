@@ -3,19 +3,21 @@
 //   1. Stable LSD radix sort of the visible (primitive, view) pairs by float32 centre
 //      depth.  The first pass reads the dense per-(view, primitive) key array, drops
 //      culled entries and materialises the pair index as the value, so ties keep the
-//      primitive order within a view.
-//   2. Two-level, load-balanced expansion in that order: each pair -> the tile rows of its
-//      screen rectangle; each row -> the tiles of the row whose pixel centres can meet the
-//      pair's support ellipse (an exact conic test, so tiles the support misses get no
-//      instance); each tile -> one instance (global tile id, sorted pair position).
-//   3. Stable LSD radix sort of the instances by tile id -> per tile, depth order.
-//   4. Per-tile [start, end) ranges.
+//      primitive order within a view; the last pass leaves each pair's tile-row count in
+//      place of its key.
+//   2. Support rows: each pair -> the tile rows of its screen rectangle; each row -> the
+//      run of tiles whose pixel centres can meet the pair's support (the band of a bounded
+//      ellipse, or an exact conic test tile by tile), with per-tile-row instance totals.
+//   3. Stable LSD radix sort of the non-empty rows by global tile row (depth order kept
+//      inside a tile row).
+//   4. Per tile row, in chunks of rows: the rows expanded into per-tile instance lists in
+//      depth order, and the per-tile [start, end) ranges.
 //
 // The radix sort is reduce-then-scan (upsweep histogram, one-CTA scan, downsweep
 // scatter) with persistent CTAs that own contiguous tile ranges: no CTA ever waits on
 // another.  The upsweep counts runs of equal digits per thread; ranking inside a tile is
-// stable (warp match + per-warp counters) and the scatter goes through shared memory so
-// that global writes are coalesced runs.
+// stable (warp multi-split by digit-bit ballots + per-warp counters) and the scatter goes
+// through shared memory so that global writes are coalesced runs.
 #include "raygs_internal.cuh"
 
 namespace raygs {
@@ -205,7 +207,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
       const uint32_t k = key[r];
       const bool valid = ok && !(p.filter && k == kCulled);
       uint32_t d = (k >> p.shift) & (R - 1);
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : uint32_t(R + lane));
+      // lanes holding the same digit: one ballot per digit bit (warp-level multi-split)
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int bit = 0; bit < BITS; ++bit) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+        peers &= ((d >> bit) & 1u) ? bal : ~bal;
+      }
+      if (!valid) peers = 1u << lane;
       uint32_t c = valid ? s_cnt[warp][d] : 0u;
       __syncwarp();
       if (valid && lane == 31 - __clz(peers)) s_cnt[warp][d] = c + __popc(peers);
