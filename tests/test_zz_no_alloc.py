@@ -66,3 +66,25 @@ def test_noalloc_rejects_scene_beyond_scratch(rg):
     assert status == 2  # RAYGS_ERR_CAPACITY, refused before any work
     torch.cuda.synchronize()
     assert float(rgb.min()) == -1.0 and float(rgb.max()) == -1.0   # outputs untouched
+
+
+def test_noalloc_gs_divergence_and_exact_refusal(rg):
+    """The GS divergence runs through the fixed array too (same image as the plan path);
+    exact anti-aliasing views need the second record buffer and are refused."""
+    import torch
+    scene = scenes.uniform_scene(1500, seed=33)
+    cams = [scenes.make_camera(64, 48, 60.0, 60.0)]
+    st = rg.scene_to_device(scene)
+    ref = rg.Renderer(cams, 1500, divergence=1)
+    rgb0, T0, nc0 = ref.forward(st)
+    torch.cuda.synchronize()
+    rgb, T, nc = _outputs(torch, ref.num_pixels)
+    status = rg.raygs_render_noalloc(cams, rg.make_scene(st), rg.make_config(divergence=1), rgb, T, nc, check=False)
+    assert status == 0, rg.lib().raygs_status_string(status)
+    torch.cuda.synchronize()
+    assert float((rgb - rgb0).abs().max()) <= TOL and float((T - T0).abs().max()) <= TOL
+    assert torch.equal(nc, nc0)
+    rgb, T, nc = _outputs(torch, ref.num_pixels)
+    status = rg.raygs_render_noalloc([dict(cams[0], mip="exact")], rg.make_scene(st), None, rgb, T, nc,
+                                     check=False)
+    assert status == 1  # RAYGS_ERR_INVALID_ARG
