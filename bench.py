@@ -39,7 +39,7 @@ WORKLOAD = ("stereo-VR batch: 3M blob primitives (10% axis ratio > 1e3), 16 view
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/render_kernel_*),
 # keyed by tile shape and a digest of the rasteriser's sources: a kernel changed since the
 # capture reports null.
-RENDER_TRAFFIC = {("16x16/b1", "d340f91bfa99a378"): 829.79e6 + 888.90e6}
+RENDER_TRAFFIC = {("16x16/b1", "8b4eaa1506de33b9"): 837.03e6 + 891.67e6}
 RENDER_SOURCES = ("render.cu", "raster_math.cuh", "raygs_internal.cuh")
 
 

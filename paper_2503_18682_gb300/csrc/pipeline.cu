@@ -86,6 +86,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.cams = take(sizeof(DevCam) * size_t(n_views));
   L.counters = take(sizeof(Counters));
   L.evals = take(2 * sizeof(unsigned long long));
+  L.tilectr = take(16);
   L.tscan = take(2 * sizeof(unsigned long long));
   L.depth = take(4 * VN);
   L.rect = take(8 * VN);
@@ -328,7 +329,12 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
     if (e != cudaSuccess) return e;
   }
   if (P.recx) return launch_render_mipx(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);
-  return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.cfg.batch_records, w.tiles, count, st);
+  if (w.tiles == 0) return cudaSuccess;
+  P.tile_counter = w.at<unsigned int>(w.L.tilectr);
+  P.n_tiles = int(w.tiles);
+  cudaError_t e = cudaMemsetAsync(P.tile_counter, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  return launch_render(P, w.cfg.tile_w, w.cfg.tile_h, w.cfg.batch_records, w.num_sms, count, st);
 }
 
 cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T_final, const int32_t *n_contrib,

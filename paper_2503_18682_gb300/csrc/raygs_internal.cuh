@@ -257,6 +257,8 @@ struct RenderParams {
   const Rec *rec;
   float t_stop, alpha_max;
   float qmix;  // 1: D_ray fragment formula, D ~ q / (q + r); 0: D_gs, D ~ q (records with h = 0)
+  unsigned int *tile_counter;  // next unclaimed tile of the persistent rasteriser (zeroed per launch)
+  int n_tiles;
   const Rec *recx;  // exact anti-aliasing: second half of each record (then rec holds the first)
   float p_min;
   float *rgb;
@@ -325,7 +327,7 @@ cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters 
 cudaError_t launch_expand(const ExpandParams &E, cudaStream_t st);
 int expand_chunk_rows(int64_t cap, int max_tiles_x);
 int64_t expand_max_chunks(int64_t trows, int64_t cap, int chunk_rows);
-cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
+cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int num_sms,
                           bool count, cudaStream_t st);
 cudaError_t launch_render_mipx(const RenderParams &P, int tile_w, int tile_h, int64_t n_tiles, bool count,
                                cudaStream_t st);
@@ -338,7 +340,7 @@ cudaError_t launch_resolve(const float *rgb_hi, const float *T_hi, float *rgb_lo
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t cams, counters, evals, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
+  size_t tilectr, cams, counters, evals, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
       seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, cbase, ccnt, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };

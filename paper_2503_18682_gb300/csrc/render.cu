@@ -1,8 +1,8 @@
 // Per-tile rasterisation and front-to-back compositing (Sec. 3 Eq. rendering and
 // Eq. rend_opacity; Sec. 4.2 fragment formula).
 //
-// One CTA per screen tile of any view; each thread shades PX consecutive pixels of a
-// tile row.  The tile's instance list (depth order) is consumed in batches: each thread
+// Persistent CTAs (one per resident slot) claim the screen tiles of all views from a
+// counter, one at a time; each thread shades PX pixels of a tile row.  A tile's instance list (depth order) is consumed in batches: each thread
 // stages records in shared memory, converting the projected centre to a tile-relative
 // offset in double-float so that per-pixel offsets stay exact to the float32 rounding of
 // the offset itself.  Per pixel, with delta = pixel centre - projected centre:
@@ -31,9 +31,14 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
   constexpr int QX = TW / PX;       // threads per tile row
   __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
   __shared__ Rec s_raw[NB];
-  __shared__ int s_view;
-  const int tile = blockIdx.x;
+  __shared__ int s_view, s_tile;
   const int tid = threadIdx.x;
+  // persistent CTAs: each claims the next tile until none is left
+  for (;;) {
+  if (tid == 0) s_tile = int(atomicAdd(P.tile_counter, 1u));
+  __syncthreads();
+  const int tile = s_tile;
+  if (tile >= P.n_tiles) break;
   if (tid == 0) {
     int v = 0;
     while (v + 1 < P.n_views && P.cams[v + 1].tile_base <= tile) ++v;
@@ -163,17 +168,34 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
       atomicAdd(&P.eval_counts[1], n_comp);
     }
   }
+  __syncthreads();  // shared state and s_tile are free before the next claim
+  }
 }
 
-cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int64_t n_tiles,
+// One CTA per resident slot (occupancy of the instantiation x SMs), at most one per tile.
+template <typename K>
+static unsigned persistent_grid(K kernel, int threads, int num_sms, int n_tiles) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long g = (long long)per_sm * (long long)(num_sms > 0 ? num_sms : 1);
+  return unsigned(g < n_tiles ? g : n_tiles);
+}
+
+cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int num_sms,
                           bool count, cudaStream_t st) {
-  if (n_tiles == 0) return cudaSuccess;
-  const unsigned grid = unsigned(n_tiles);
-#define RAYGS_RENDER_CASE(TW, TH, PX, NBF)                                                      \
-  if (tile_w == TW && tile_h == TH && batch_records == NBF) {                                  \
-    if (count) render_kernel<TW, TH, PX, NBF, true><<<grid, TW * TH / PX, 0, st>>>(P);         \
-    else render_kernel<TW, TH, PX, NBF, false><<<grid, TW * TH / PX, 0, st>>>(P);              \
-    return cudaGetLastError();                                                                 \
+  if (P.n_tiles <= 0) return cudaSuccess;
+#define RAYGS_RENDER_CASE(TW, TH, PX, NBF)                                                             \
+  if (tile_w == TW && tile_h == TH && batch_records == NBF) {                                         \
+    constexpr int NT = TW * TH / PX;                                                                  \
+    if (count) {                                                                                      \
+      auto k = render_kernel<TW, TH, PX, NBF, true>;                                                  \
+      k<<<persistent_grid(k, NT, num_sms, P.n_tiles), NT, 0, st>>>(P);                                \
+    } else {                                                                                          \
+      auto k = render_kernel<TW, TH, PX, NBF, false>;                                                 \
+      k<<<persistent_grid(k, NT, num_sms, P.n_tiles), NT, 0, st>>>(P);                                \
+    }                                                                                                 \
+    return cudaGetLastError();                                                                        \
   }
   RAYGS_RENDER_CASE(16, 16, 4, 1)
   RAYGS_RENDER_CASE(16, 8, 4, 1)
