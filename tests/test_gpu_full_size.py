@@ -81,3 +81,38 @@ def test_stereo_batch_gs_divergence_sampled(oracle_lib, stereo):
     scene, cams, st = stereo
     r, rgb, T = graph_render(cams, st, scene["means"].shape[0], divergence=1)
     check_sampled(oracle_lib, scene, cams, r, rgb, T, per_view=32, ocfg=dict(divergence=1))
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_precision_workload_full_size_sampled(oracle_lib, dt):
+    """The 6M-primitive precision workload at full size (4 views at 3840x2160 and the same
+    poses at 960x540 with the MIP filter), SH and log-scales stored in FP16 / BF16 and
+    opacity in FP16: the reduced form is bit-equal to the FP32 form of the widened stored
+    values, and 48 sampled pixels per view match the oracle on those values."""
+    import torch
+    from paper_2503_18682_gb300 import build, raygs
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    scene, cams = scenes.workload_precision()
+    red = scenes.to_storage(scene, dt)
+    wide = scenes.widen(red)
+    del scene
+    n = red["means"].shape[0]
+    outs = []
+    for sc in (red, wide):
+        r = raygs.Renderer(cams, n)
+        rgb, T, _ = r.forward(raygs.scene_to_device(sc))
+        torch.cuda.synchronize()
+        outs.append((r, rgb.cpu().numpy(), T.cpu().numpy()))
+        del rgb, T
+        torch.cuda.empty_cache()
+    (r, rgb_red, T_red), (_, rgb_wide, T_wide) = outs
+    assert np.array_equal(rgb_red, rgb_wide) and np.array_equal(T_red, T_wide)
+    stats = []
+    for v, cam in enumerate(cams):
+        sl = view_slice(r, v)
+        pix, idx = sample_pixels(cam, 48, seed=200 + v)
+        orc = oracle_lib.render(wide, cam, pixels=pix)
+        stats.append(compare(rgb_red[sl][idx].astype(np.float64), T_red[sl][idx].astype(np.float64), orc))
+    assert_parity_sampled(stats)
