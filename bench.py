@@ -72,10 +72,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, path=None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"raygs_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -342,7 +343,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         elapsed = headline(len(plans), args.steps)
         torch.cuda.synchronize()
         barrier(world)
@@ -724,6 +725,7 @@ def main():
     ap.add_argument("--n", type=int, default=3_000_000)
     ap.add_argument("--ref-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="keep the raw clock samples of the timed region here")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the FP16/BF16 storage measurement on the 6M-primitive 4K workload")
