@@ -189,24 +189,32 @@ int64_t raygs_plan_num_tiles(const raygs_plan *plan);           /* screen tiles,
  * Sec. 5 Eq. mip; Sec. 4.1 and App. A.1-A.3 quad V_ray -> screen tile rectangle; the
  * per-pixel factors of the fragment formula of Sec. 4.2 / App. A.4; colour from SH).
  * With RAYGS_DIV_GS the records instead hold Sigma_pi^-1 of Sec. 3.1 and the tile
- * rectangle bounds the screen ellipse of the EWA support.  Reads the scene, writes per-(primitive, view) depth keys, tile rectangles and 64-byte
- * pixel records into the workspace.  Requires a bound plan and scene->n == n_gaussians.
+ * rectangle bounds the screen ellipse of the EWA support.  With RAYGS_MIP_EXACT views the
+ * record is 128 bytes (the per-pixel forms of the exact anti-aliasing) and the rectangle
+ * bounds the support of the primitive inflated by a bound of the per-ray smoothing.
+ * Reads the scene, writes per-(primitive, view) depth keys, tile rectangles, support
+ * ellipses and pixel records into the workspace.  Requires a bound plan and
+ * scene->n == n_gaussians.
  */
 raygs_status raygs_preprocess(raygs_plan *plan, const raygs_scene *scene, void *stream);
 
 /*
  * Binning for Eq. rendering's depth order: stable on-device radix sort of the visible
- * (primitive, view) pairs by float32 centre depth (ties keep primitive order), emission of
- * one instance per covered tile in that order, stable radix sort of instances by tile id,
- * and per-tile [start, end) ranges.  Requires raygs_preprocess on the same stream first.
+ * (primitive, view) pairs by float32 centre depth (ties keep primitive order); per pair and
+ * tile row of its rectangle, the run of tiles whose pixel centres can meet its support;
+ * stable radix sort of those rows by global tile row; per tile row, the expansion of its
+ * rows into per-tile instance lists in depth order and the per-tile [start, end) ranges.
+ * The instance total and an overflow flag go to device counters.  Requires
+ * raygs_preprocess on the same stream first.
  */
 raygs_status raygs_bin_sort(raygs_plan *plan, void *stream);
 
 /*
  * Per-tile rasterisation: for every pixel, the ray-maximum divergence D_ray in closed form
- * (Sec. 4.2 fragment formula with the quad coordinate obtained from the pixel ray),
- * omega = min(alpha_max, o exp(-D/2)) when D <= kappa (Eq. rend_opacity, Eq. support), and
- * front-to-back compositing (Eq. rendering) stopping before T < t_stop.
+ * (Sec. 4.2 fragment formula with the quad coordinate obtained from the pixel ray; D_gs of
+ * Sec. 3.1 with RAYGS_DIV_GS; the exact anti-aliased form of Sec. 5 for RAYGS_MIP_EXACT
+ * views), omega = min(alpha_max, o exp(-D/2)) when D <= kappa (Eq. rend_opacity, Eq.
+ * support), and front-to-back compositing (Eq. rendering) stopping before T < t_stop.
  *   rgb       [num_pixels][3] float32 device, required
  *   T_final   [num_pixels]    float32 device, optional (NULL): final transmittance
  *   n_contrib [num_pixels]    int32 device, optional (NULL): 1 + position of the last
