@@ -63,6 +63,11 @@ def test_plan_validation_host_only(rg):
         dict(n=-1), dict(n=1 << 31), dict(cap=-5),
         dict(cfg=dict(tile_w=12)), dict(cfg=dict(p_min=0.0)), dict(cfg=dict(alpha_max=1.0)),
         dict(cam=dict(width=0)), dict(cam=dict(fx=0.0)), dict(cam=dict(near=0.0)),
+        # mode combinations the header refuses: GS with backward or with an anti-aliasing
+        # term, an unknown divergence or anti-aliasing mode, a batch mixing exact views
+        dict(cfg=dict(divergence=1, enable_backward=1)), dict(cfg=dict(divergence=1), cam=dict(mip=1)),
+        dict(cfg=dict(divergence=1), cam=dict(mip=2)), dict(cfg=dict(divergence=2)),
+        dict(cam=dict(mip=3)), dict(cfg=dict(batch_records=3)),
     ]
     for b in bad:
         cam = dict(cams[0], **b.get("cam", {}))
@@ -72,6 +77,13 @@ def test_plan_validation_host_only(rg):
                                         C.byref(cfg), C.byref(h))
         assert st == 1, b
         assert not h.value
+    h = C.c_void_p()
+    mixed = [dict(cams[0], mip="exact"), cams[0]]
+    assert rg.lib().raygs_plan_create(rg.make_cameras(mixed), 2, 10, 10, None, C.byref(h)) == 1
+    for ok in ([dict(cams[0], mip="exact")] * 2, [dict(cams[0], mip=1), cams[0]]):
+        h = C.c_void_p()
+        assert rg.lib().raygs_plan_create(rg.make_cameras(ok), 2, 10, 10, None, C.byref(h)) == 0
+        rg.lib().raygs_plan_destroy(h)
     h = C.c_void_p()
     assert rg.lib().raygs_plan_create(rg.make_cameras(cams), 0, 10, 10, None, C.byref(h)) == 1
     assert rg.lib().raygs_plan_create(rg.make_cameras(cams * 65), 65, 10, 10, None, C.byref(h)) == 1
