@@ -220,6 +220,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     pk = peaks()
 
+    if args.mode == "profile" and args.workload == "backward":
+        return profile_backward(args, rank, dev)
     if args.workload == "mip720":
         scene, cams = scenes.workload_mip_720p()
     else:
@@ -237,10 +239,15 @@ def run_ours(args, world, rank, local):
         rgb, T, nc = r.alloc_outputs()
         r.forward(st, rgb, T, nc)
         sc = raygs.make_scene(st)
-        for _ in range(args.warmup + args.steps):
+        for i in range(args.warmup + args.steps):
+            last = i == args.warmup + args.steps - 1
+            if last:
+                torch.cuda.nvtx.range_push("pass")  # the last pass, for ncu --nvtx-include pass/
             raygs.raygs_preprocess(r.plan, sc)
             raygs.raygs_bin_sort(r.plan)
             raygs.raygs_render(r.plan, rgb, T, nc)
+            if last:
+                torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps(dict(mode="profile", workload=args.workload, passes=args.warmup + args.steps,
@@ -658,6 +665,42 @@ def precision_storage(args, dev):
     return out
 
 
+def profile_backward(args, rank, dev):
+    """For ncu: the forward + backward of the 1.5M-primitive 1280x720 view, W + K passes after
+    one sizing pass; the last pass inside the NVTX range "pass"."""
+    import torch
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene, cams = scenes.workload_backward_720p()
+    st = raygs.scene_to_device(scene, dev)
+    n = scene["means"].shape[0]
+    r = raygs.Renderer(cams, n, device=dev, enable_backward=1)
+    rgb, T, nc = r.forward(st)
+    g_rgb = torch.ones_like(rgb)
+    sc = raygs.make_scene(st)
+    grads = {k: torch.empty((n, d), dtype=torch.float32, device=dev) for k, d in
+             (("means", 3), ("log_scales", 3), ("quats", 4))}
+    grads["opacity_logits"] = torch.empty(n, dtype=torch.float32, device=dev)
+    grads["sh"] = torch.empty(st["sh"].shape, dtype=torch.float32, device=dev)
+    G = raygs.Grads()
+    G.d_means, G.d_log_scales, G.d_quats = (grads["means"].data_ptr(), grads["log_scales"].data_ptr(),
+                                            grads["quats"].data_ptr())
+    G.d_opacity_logits, G.d_sh = grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr()
+    for i in range(args.warmup + args.steps):
+        last = i == args.warmup + args.steps - 1
+        if last:
+            torch.cuda.nvtx.range_push("pass")
+        raygs.raygs_preprocess(r.plan, sc)
+        raygs.raygs_bin_sort(r.plan)
+        raygs.raygs_render(r.plan, rgb, T, nc)
+        raygs.raygs_render_backward(r.plan, sc, T, nc, g_rgb, None, G)
+        if last:
+            torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if rank == 0:
+        print(json.dumps(dict(mode="profile", workload="backward", passes=args.warmup + args.steps,
+                              counters=r.last_counters)), flush=True)
+
+
 def fwd_bwd_ms_per_view(args, dev):
     """Forward + backward of the 1.5M-primitive 1280x720 view (blob generator, seed 2):
     preprocess, binning, rasteriser and the full backward to all parameters, with a fixed
@@ -734,7 +777,8 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
     ap.add_argument("--in-flight", type=int, default=2,
                     help="batches in flight on separate streams (each with its own plan)")
-    ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720"])
+    ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720", "backward"],
+                    help="profile mode only: backward = forward + backward of the 1.5M-primitive 720p view")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       const float4 A = s_A[j], B = s_B[j];
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
       const float4 Cs = s_C[j];
-      const uint32_t hit = row_may_hit<PX>(A, B, Cs, s_D[j].w, fl_x, fl_y, step)
+      // as in the forward pass, the segment filter pays only at 8 pixels per thread
+      const uint32_t hit = (PX < 8 || row_may_hit<PX>(A, B, Cs, s_D[j].w, fl_x, fl_y, step))
                                ? eval_pixels<PX>(A, B, Cs.x, fl_x, fl_y, step, q, r, y0, y1, y2)
                                : 0u;
       float acc[kGradW];
