@@ -209,29 +209,43 @@ cudaError_t launch_render_backward(const BackParams &P, int tile_w, int tile_h, 
   return cudaErrorInvalidValue;
 }
 
-// Sum of the partials of each (primitive, view) pair: one warp per sorted pair, over the
-// contiguous run of its instances in emission order.
+// Sum of the partials of each (primitive, view) pair over the contiguous run of its
+// instances in emission order: eight lanes per sorted pair (four pairs per warp; a pair has
+// about six instances on the 720p workload), then an xor reduction inside each group of
+// eight lanes, whose lanes write the 13 totals.
 __global__ void __launch_bounds__(256) pair_grads_kernel(PairGradParams P) {
+  constexpr int GL = 8;  // lanes per pair
   const uint32_t nvis = P.counters->n_visible;
   const uint32_t ninst = P.counters->n_inst_clamped;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nvis; p += warps) {
-    const uint32_t e0 = P.seg_off[P.row_off[p]];
-    const uint32_t e1 = p + 1 < nvis ? P.seg_off[P.row_off[p + 1]] : ninst;
+  const int lane = threadIdx.x & 31, sl = lane & (GL - 1);
+  const uint32_t groups = (gridDim.x * blockDim.x) / GL;
+  const uint32_t g0 = (blockIdx.x * blockDim.x + threadIdx.x) / GL;
+  // every lane of a warp runs the same number of iterations (full-warp shuffles)
+  const uint32_t iters = (nvis + groups - 1) / groups;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint32_t p = g0 + it * groups;
     float acc[kGradW];
 #pragma unroll
     for (int c = 0; c < kGradW; ++c) acc[c] = 0.f;
-    for (uint32_t e = e0 + lane; e < e1; e += 32) {
+    if (p < nvis) {
+      const uint32_t e0 = P.seg_off[P.row_off[p]];
+      const uint32_t e1 = p + 1 < nvis ? P.seg_off[P.row_off[p + 1]] : ninst;
+      for (uint32_t e = e0 + sl; e < e1; e += GL) {
 #pragma unroll
-      for (int c = 0; c < kGradW; ++c) acc[c] += P.partials[size_t(e) * kGradW + c];
+        for (int c = 0; c < kGradW; ++c) acc[c] += P.partials[size_t(e) * kGradW + c];
+      }
     }
-    float v16[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v16[c] = c < kGradW ? acc[c] : 0.f;
-    const float tot = warp_sum16(v16, lane);
-    const int c = warp_sum16_component(lane);
-    if ((lane & 1) == 0 && c < kGradW) P.pg[size_t(P.pairs[p]) * kGradW + c] = tot;
+    for (int o = GL / 2; o >= 1; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < kGradW; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    }
+    if (p < nvis) {
+      float *dst = P.pg + size_t(P.pairs[p]) * kGradW;
+#pragma unroll
+      for (int c = 0; c < kGradW; ++c)
+        if (c % GL == sl) dst[c] = acc[c];
+    }
   }
 }
 
