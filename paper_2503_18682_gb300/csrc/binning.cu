@@ -337,16 +337,15 @@ __global__ void __launch_bounds__(256) hist_offsets_kernel(uint32_t *hist, int n
 }
 
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
-  const int n = (p.bits == 9 ? 512 : 256) * p.G;
+  if (p.bits != 8) return cudaErrorInvalidValue;  // every pass uses 8-bit digits
+  const int n = 256 * p.G;
   const int nb = (n + kHistBlock - 1) / kHistBlock;
   uint32_t *bsum = p.hist + n;  // scratch after the histogram (the layout reserves 512*G + G)
-  if (p.bits == 9) sort_upsweep<9><<<p.G, kSortThreads, 0, st>>>(p);
-  else sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
   hist_reduce_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
   hist_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nb, p.d_total);
   hist_offsets_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
   if (p.wide) sort_downsweep<8, true><<<p.G, kSortThreads, 0, st>>>(p);
-  else if (p.bits == 9) sort_downsweep<9, false><<<p.G, kSortThreads, 0, st>>>(p);
   else sort_downsweep<8, false><<<p.G, kSortThreads, 0, st>>>(p);
   return cudaGetLastError();
 }

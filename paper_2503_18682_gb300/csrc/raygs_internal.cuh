@@ -177,7 +177,7 @@ struct SortPass {
   const uint32_t *d_count;  // device item count (nullable: count_max is used)
   uint32_t count_max;
   int shift;
-  int bits;                 // digit width of this pass (8 or 9)
+  int bits;                 // digit width of this pass (8)
   int filter;               // drop kCulled keys; value = item index
   uint32_t *hist;           // [512][G]
   int G;
