@@ -390,6 +390,7 @@ def run_ours(args, world, rank, local):
     # 8-B tile rectangle and 32-B support ellipse written; the 4-B key of every pair
     attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
     prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
+    bin_bytes = binning_bytes(ctr, n * len(cams))
     # kernels per pass: preprocess (2), depth sort (4 passes x 5), row-count scan (3),
     # row spans (1), tile-row instance scan (1), tile-row sort (passes x 5), tile-row
     # ranges (1), chunk scan + chunk counts + instance lists (3), rasteriser (1)
@@ -412,7 +413,10 @@ def run_ours(args, world, rank, local):
         evaluated_pairs=evals, composited_pairs=comps,
         n_visible=ctr["n_visible"], n_instances=ctr["n_instances"],
         stages=dict(stages, preprocess_hbm_gbs=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9,
-                    preprocess_hbm_frac=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"]),
+                    preprocess_hbm_frac=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    bin_sort_bytes=bin_bytes,
+                    bin_sort_hbm_gbs=bin_bytes / (stages["bin_sort_ms"] * 1e-3) / 1e9,
+                    bin_sort_hbm_frac=bin_bytes / (stages["bin_sort_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"]),
         autotune=tuned,
         roofline=dict(bound="alu", kernel=f"render_kernel<{r.cfg.tile_w},{r.cfg.tile_h}>", achieved=ach_tf, peak=peak_tf,
                       unit="TFLOP/s", frac=ach_tf / peak_tf,
@@ -663,6 +667,24 @@ def precision_storage(args, dev):
         torch.cuda.empty_cache()
     out["workload"] = f"{n} blob primitives, 4 views 3840x2160 + the same 4 poses at 960x540 with MIP"
     return out
+
+
+def binning_bytes(ctr, pairs):
+    """Algorithmic bytes of one binning pass (each array read or written once per use; the
+    row payload as stored): depth sort (the dense 4-B keys read, then 8 B per visible pair
+    per pass in and out, the upsweeps' key reads, the last pass's 8-B rectangle gather),
+    support rows (the 32-B support sector per pair, 16 B written per row), the tile-row
+    sort (4-B key + 8-B payload + 4-B length read per row in the first pass, 12 B written per
+    kept row, 24 B per kept row in the second pass, the upsweeps' key reads), the tile-row
+    ranges and chunk counts (the sorted keys read twice), and the expansion (8-B payload read
+    per kept row, 4 B written per instance)."""
+    nv, nr, nk, ni = (int(ctr[k]) for k in ("n_visible", "n_rows", "n_rows_kept", "n_instances"))
+    depth = 4 * pairs + 8 * nv + 3 * 16 * nv + 8 * nv + 4 * pairs + 3 * 4 * nv
+    rows = 32 * nv + 16 * nr
+    row_sort = 16 * nr + 12 * nk + 24 * nk + 4 * nr + 4 * nk
+    ranges = 2 * 4 * nk
+    expand = 8 * nk + 4 * ni
+    return depth + rows + row_sort + ranges + expand
 
 
 def profile_backward(args, rank, dev):
