@@ -430,16 +430,26 @@ def run_ours(args, world, rank, local):
                  one_batch_at_a_time=dict(value=1e3 / e2e_single_ms, ms_per_step=e2e_single_ms)),
         gpu_launches=int(gpu_launches),
     )
+    def context(key, fn):
+        """A context measurement beside the headline: a failure (say, out of memory on a
+        smaller device) is recorded in its key instead of losing the line."""
+        try:
+            line[key] = fn()
+        except Exception as ex:  # noqa: BLE001 - reported, not hidden
+            line[key] = dict(error=f"{type(ex).__name__}: {str(ex)[:300]}")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     if not args.no_backward:
-        line["fwd_bwd"] = fwd_bwd_ms_per_view(args, dev)
+        context("fwd_bwd", lambda: fwd_bwd_ms_per_view(args, dev))
     if not args.no_precision:
         del plans[1:]
         plan_outputs.clear()
         torch.cuda.empty_cache()
-        line["gs_vs_raygs"] = dict(stereo_batch=divergence_ab(st, cams, n, r.cfg, r.capacity, dev),
-                                   plain_720p=divergence_ab_720p(r.cfg, dev))
-        line["precision_storage"] = precision_storage(args, dev)
-        line["antialiasing"] = antialiasing(args, dev)
+        context("gs_vs_raygs", lambda: dict(stereo_batch=divergence_ab(st, cams, n, r.cfg, r.capacity, dev),
+                                            plain_720p=divergence_ab_720p(r.cfg, dev)))
+        context("precision_storage", lambda: precision_storage(args, dev))
+        context("antialiasing", lambda: antialiasing(args, dev))
     if rank == 0 and not args.no_cpu_baseline:
         spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
