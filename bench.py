@@ -423,7 +423,9 @@ def run_ours(args, world, rank, local):
                       traffic=RENDER_TRAFFIC.get((f"{r.cfg.tile_w}x{r.cfg.tile_h}/b{r.cfg.batch_records}",
                                                   render_source_digest())),
                       peak_note=f"FP32 {sms} SMs x 128 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz (derived)",
-                      algorithmic=f"{FLOP_EVAL} flop per evaluated pair + {FLOP_COMP} per composited pair"),
+                      algorithmic=f"{FLOP_EVAL} flop per evaluated pair + {FLOP_COMP} per composited pair",
+                      timing="raygs_render launches (the rasteriser alone) timed with CUDA events on the plan's "
+                             "stream, mean of 5 after warm-up; pairs counted by the instrumented variant"),
         clocks=clocks,
         e2e=dict(value=1e3 / e2e_ms, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
                  ms_per_step=e2e_ms, batches_in_flight=min(2, len(plans)),
