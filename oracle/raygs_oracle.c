@@ -530,6 +530,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
         const double tau = n0 / d0;
         if (!(tau > 0)) continue;
         const double cth = 1.0 / xn; /* cos of the ray's angle to the optical axis */
+        /* lambda = sigma_x^2 tau(x)^2 with sigma_x^2 = sigma^2 cos^3(theta) / (fx fy), the
+         * pixel's area at unit distance along the ray */
         const double lam = sig2 * cth * cth * cth * tau * tau;
         double n1 = 0, d1 = 0, ratio = 1;
         for (int j = 0; j < 3; ++j) {
@@ -545,6 +547,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
           const double r = tauh * a[j] - b[j];
           D += r * r / (g->s[j] * g->s[j] + lam);
         }
+        /* modulation sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x)):
+         * ratio = |Sigma| / |Sigma^_x|, d0 = x^T Sigma^-1 x, d1 = x^T Sigma^_x^-1 x (unit x) */
         mod = sqrt(ratio * d0 / d1);
       } else if (gs_div) {
         /* Sec. 3.1: (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), pi(x) the pixel centre */
