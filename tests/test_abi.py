@@ -94,3 +94,10 @@ def test_status_strings(rg):
         assert rg.lib().raygs_status_string(s)
     with pytest.raises(rg.RayGSError):
         rg._check(1, "x")
+    # no CUDA call of this thread has failed through the library (host-only calls above)
+    import threading
+    seen = []
+    th = threading.Thread(target=lambda: seen.append(rg.lib().raygs_last_cuda_error()))
+    th.start()
+    th.join()
+    assert seen == [0]
