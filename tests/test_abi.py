@@ -94,7 +94,7 @@ def test_status_strings(rg):
         assert rg.lib().raygs_status_string(s)
     with pytest.raises(rg.RayGSError):
         rg._check(1, "x")
-    # no CUDA call of this thread has failed through the library (host-only calls above)
+    # the failed-CUDA-call record is per thread and starts clear in a new thread
     import threading
     seen = []
     th = threading.Thread(target=lambda: seen.append(rg.lib().raygs_last_cuda_error()))
