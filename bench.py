@@ -236,8 +236,10 @@ def run_ours(args, world, rank, local):
 
     if args.mode == "profile" and args.workload == "backward":
         return profile_backward(args, rank, dev)
-    if args.workload == "mip720":
+    if args.workload in ("mip720", "mip720exact"):
         scene, cams = scenes.workload_mip_720p()
+        if args.workload == "mip720exact":
+            cams = [dict(c, mip="exact") for c in cams]
     else:
         scene, cams = scenes.workload_stereo_batch(n=args.n)
     n = int(scene["means"].shape[0])
@@ -825,8 +827,9 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
     ap.add_argument("--in-flight", type=int, default=2,
                     help="batches in flight on separate streams (each with its own plan)")
-    ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720", "backward"],
-                    help="profile mode only: backward = forward + backward of the 1.5M-primitive 720p view")
+    ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720", "mip720exact", "backward"],
+                    help="profile mode only: mip720exact = the 720p workload with the exact anti-aliasing; "
+                         "backward = forward + backward of the 1.5M-primitive 720p view")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
