@@ -108,7 +108,10 @@ typedef struct {
   int32_t fp64_degenerate; /* FP64 vertex stage for near-degenerate primitives (scale
                               ratio max/min > degenerate_ratio): 0 never; 1 (default) in
                               the views where the float32 solve is ill-conditioned (seen
-                              nearly edge-on); 2 in every view where they are visible */
+                              nearly edge-on); 2 in every view where they are visible.
+                              Whatever the setting, a pair whose skip decision (opacity at
+                              the cut-off, camera inside, Sec. 3.2 Eq. c) lies within the
+                              float32 rounding of its threshold is decided in FP64 */
   float degenerate_ratio; /* 1e3 */
   int32_t enable_backward; /* 1: reserve workspace for raygs_render_backward (default 0) */
   int32_t batch_records;  /* records the rasteriser stages in shared memory per thread and
@@ -310,9 +313,9 @@ size_t raygs_autotune_workspace_bytes(const raygs_camera *cams, int32_t n_views,
  *    (primitive, tile) instances.  A problem that does not fit is rejected with
  *    RAYGS_ERR_CAPACITY before any work is enqueued; one whose instances overflow the
  *    remaining space returns RAYGS_ERR_CAPACITY after the render (image incomplete).
- *  - Set-up: the first call on each device, with that device current, looks up the
- *    array's device address (which loads the module on that device); make that first call
- *    before any stream capture on that device.
+ *  - Set-up: every call, with the caller's device current, looks up the array's device
+ *    address in that device's context; the first call on a device also loads the module
+ *    there, so make that first call before any stream capture on that device.
  *  - The call reads a device counter at the end and therefore synchronises `stream`.
  *  - Every call shares the one array, which keeps the last call's contents (the call
  *    clears what must start at zero).  Calls that overlap on the GPU (different streams or

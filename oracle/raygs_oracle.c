@@ -83,7 +83,7 @@ enum {
   OG_RGB = 8,      /* colour (3) */
   OG_S = 11,       /* scales after the anti-aliasing term (3) */
   OG_RC = 14,      /* camera-frame rotation R_c (9, row-major) */
-  OG_BORDER = 23,  /* 1 when a cull decision sits within 1e-5 (relative) of its threshold */
+  OG_BORDER = 23,  /* 1 when a skip decision sits within FP64 rounding of its threshold */
   OG_LEN = 24
 };
 
@@ -346,32 +346,45 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
     Rtmu[k] = g->Rc[k] * g->mu[0] + g->Rc[3 + k] * g->mu[1] + g->Rc[6 + k] * g->mu[2];
 
   const int gs_div = (int)cfg[CFG_DIV] == 1;
+  /* Rounding model of the two skip decisions below.  Two FP64 evaluations of this stage
+   * (this one and a renderer's) differ mainly through the camera-frame mean, which may
+   * carry a relative error up to E_MU; R_c^T mu then moves by up to E_MU |mu|_1 per axis,
+   * and m_k = (R_c^T mu)_k / s_k by that over s_k (large for thin primitives seen from
+   * near their plane). */
+  const double E_MU = 1e-11;
+  const double mu1 = fabs(g->mu[0]) + fabs(g->mu[1]) + fabs(g->mu[2]);
+  double rel_o = 1e-12; /* relative rounding bound of the opacity */
   if ((int)cam[CAM_MIP] == 1) {
     /* Eq. mip with the pixel-invariant Sigma^ = Sigma + lambda I */
     double mu2 = g->mu[0] * g->mu[0] + g->mu[1] * g->mu[1] + g->mu[2] * g->mu[2];
     double lam = cfg[CFG_MIPS2] * mu2 / (cam[CAM_FX] * cam[CAM_FY]);
-    double c2 = 0, c2h = 0, det = 1, deth = 1;
+    double c2 = 0, c2h = 0, det = 1, deth = 1, e2 = 0, e2h = 0;
     for (int k = 0; k < 3; ++k) {
       double sh2 = s2[k] + lam;
       c2 += Rtmu[k] * Rtmu[k] / s2[k];
       c2h += Rtmu[k] * Rtmu[k] / sh2;
+      e2 += 2.0 * fabs(Rtmu[k]) * E_MU * mu1 / s2[k];
+      e2h += 2.0 * fabs(Rtmu[k]) * E_MU * mu1 / sh2;
       det *= s2[k];
       deth *= sh2;
       s2[k] = sh2;
       g->s[k] = sqrt(sh2);
     }
     o *= sqrt(det * c2 / (deth * c2h));
+    rel_o += 0.5 * (e2 / c2 + e2h / c2h);
   }
   g->o = o;
   double pmin = cfg[CFG_PMIN];
   g->kappa = -2.0 * log(pmin / o);
-  if (fabs(o - pmin) <= 1e-5 * pmin) g->border = 1;
-  if (!(g->kappa > 0)) { g->status = 2; return; }
+  /* Eq. support: skip when kappa <= 0, i.e. o <= p_min */
+  if (fabs(log(o / pmin)) <= rel_o) g->border = 1;
 
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 3; ++j) g->W[3 * k + j] = g->Rc[3 * j + k] / g->s[k];
   for (int k = 0; k < 3; ++k) g->m[k] = Rtmu[k] / g->s[k];
   g->c2 = g->m[0] * g->m[0] + g->m[1] * g->m[1] + g->m[2] * g->m[2];
+  double e_c2 = 1e-12 * g->c2 + 2.0 * rel_o; /* + the rounding of kappa */
+  for (int k = 0; k < 3; ++k) e_c2 += 2.0 * fabs(g->m[k]) * E_MU * mu1 / g->s[k];
   if (gs_div) {
     /* Sec. 3.1: Sigma_pi = J Sigma J^T with J the Jacobian of pi(p) = (fx p_x / p_z + cx,
      * fy p_y / p_z + cy) at the camera-frame mean; Sigma = R_c S^2 R_c^T */
@@ -398,8 +411,11 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
     g->A[2] = P[0] / det;
     g->u[0] = fx * g->mu[0] / z + cam[CAM_CX];
     g->u[1] = fy * g->mu[1] / z + cam[CAM_CY];
-  } else {
-    if (fabs(g->c2 - g->kappa) <= 1e-5 * g->kappa) g->border = 1;
+  }
+  if (!(g->kappa > 0)) { g->status = 2; return; }
+  if (!gs_div) {
+    /* Sec. 3.2 Eq. c: skip when c^2 <= kappa */
+    if (fabs(g->c2 - g->kappa) <= e_c2) g->border = 1;
     if (!(g->c2 > g->kappa)) { g->status = 3; return; }
   }
 
@@ -419,6 +435,72 @@ static void prepare_one(int64_t i, const float *means, const float *log_scales,
     for (int k = 1; k < K; ++k) v += Y[k] * (double)f[3 * k + ch];
     g->rgb[ch] = v > 0 ? v : 0.0;
   }
+}
+
+/* The rendered opacity of primitive g at the pixel (px, py) with ray x, before the cut-off
+ * and the clamp: *om = o m(x) exp(-D/2) and *D_out = D, with D = D_ray (Eq. Q_ray), D_gs
+ * (Sec. 3.1) or the exact anti-aliased D_ray under Sigma^_x (Sec. 5; m(x) its modulation,
+ * else m = 1).  Returns 0 when the pixel does not count (tau <= 0). */
+static int pixel_weight(const prim *g, const double x[3], int px, int py, int mip_exact, int gs_div,
+                        double sig2, double *D_out, double *om) {
+  double D, mod = 1.0;
+  if (mip_exact) {
+    /* Sec. 5: unit ray xh, tau(xh) under Sigma, lambda = sigma_x^2 tau^2, then D_ray and
+     * the modulation under Sigma^_x = Sigma + lambda I, both in Sigma's eigenframe
+     * (Sigma = R_c diag(s^2) R_c^T, so Sigma^_x = R_c diag(s^2 + lambda) R_c^T). */
+    const double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    const double xh[3] = {x[0] / xn, x[1] / xn, x[2] / xn};
+    double a[3], b[3]; /* R_c^T xh and R_c^T mu */
+    for (int j = 0; j < 3; ++j) {
+      a[j] = g->Rc[j] * xh[0] + g->Rc[3 + j] * xh[1] + g->Rc[6 + j] * xh[2];
+      b[j] = g->Rc[j] * g->mu[0] + g->Rc[3 + j] * g->mu[1] + g->Rc[6 + j] * g->mu[2];
+    }
+    double n0 = 0, d0 = 0;
+    for (int j = 0; j < 3; ++j) {
+      const double s2 = g->s[j] * g->s[j];
+      n0 += b[j] * a[j] / s2;
+      d0 += a[j] * a[j] / s2;
+    }
+    const double tau = n0 / d0;
+    if (!(tau > 0)) return 0;
+    const double cth = 1.0 / xn; /* cos of the ray's angle to the optical axis */
+    /* lambda = sigma_x^2 tau(x)^2 with sigma_x^2 = sigma^2 cos^3(theta) / (fx fy), the
+     * pixel's area at unit distance along the ray */
+    const double lam = sig2 * cth * cth * cth * tau * tau;
+    double n1 = 0, d1 = 0, ratio = 1;
+    for (int j = 0; j < 3; ++j) {
+      const double s2 = g->s[j] * g->s[j], sh2 = s2 + lam;
+      n1 += b[j] * a[j] / sh2;
+      d1 += a[j] * a[j] / sh2;
+      ratio *= s2 / sh2;
+    }
+    const double tauh = n1 / d1;
+    if (!(tauh > 0)) return 0;
+    D = 0; /* (tauh xh - mu)^T Sigma^_x^-1 (tauh xh - mu) */
+    for (int j = 0; j < 3; ++j) {
+      const double r = tauh * a[j] - b[j];
+      D += r * r / (g->s[j] * g->s[j] + lam);
+    }
+    /* modulation sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x)):
+     * ratio = |Sigma| / |Sigma^_x|, d0 = x^T Sigma^-1 x, d1 = x^T Sigma^_x^-1 x (unit x) */
+    mod = sqrt(ratio * d0 / d1);
+  } else if (gs_div) {
+    /* Sec. 3.1: (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), pi(x) the pixel centre */
+    const double dx = (px + 0.5) - g->u[0], dy = (py + 0.5) - g->u[1];
+    D = g->A[0] * dx * dx + 2.0 * g->A[1] * dx * dy + g->A[2] * dy * dy;
+  } else {
+    double w[3];
+    for (int r = 0; r < 3; ++r) w[r] = g->W[3 * r] * x[0] + g->W[3 * r + 1] * x[1] + g->W[3 * r + 2] * x[2];
+    double num = g->m[0] * w[0] + g->m[1] * w[1] + g->m[2] * w[2]; /* x^T Si mu */
+    double den = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];          /* x^T Si x  */
+    double tau = num / den;
+    if (!(tau > 0)) return 0;
+    double r0 = tau * w[0] - g->m[0], r1 = tau * w[1] - g->m[1], r2 = tau * w[2] - g->m[2];
+    D = r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  *D_out = D;
+  *om = g->o * mod * exp(-0.5 * D);
+  return 1;
 }
 
 static int cmp_prim(const void *pa, const void *pb) {
@@ -509,62 +591,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
     uint64_t h = 1469598103934665603ull;
     for (int64_t k = 0; k < nv; ++k) {
       const prim *g = order[k];
-      double D, mod = 1.0;
-      if (mip_exact) {
-        /* Sec. 5: unit ray xh, tau(xh) under Sigma, lambda = sigma_x^2 tau^2, then D_ray and
-         * the modulation under Sigma^_x = Sigma + lambda I, both in Sigma's eigenframe
-         * (Sigma = R_c diag(s^2) R_c^T, so Sigma^_x = R_c diag(s^2 + lambda) R_c^T). */
-        const double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        const double xh[3] = {x[0] / xn, x[1] / xn, x[2] / xn};
-        double a[3], b[3]; /* R_c^T xh and R_c^T mu */
-        for (int j = 0; j < 3; ++j) {
-          a[j] = g->Rc[j] * xh[0] + g->Rc[3 + j] * xh[1] + g->Rc[6 + j] * xh[2];
-          b[j] = g->Rc[j] * g->mu[0] + g->Rc[3 + j] * g->mu[1] + g->Rc[6 + j] * g->mu[2];
-        }
-        double n0 = 0, d0 = 0;
-        for (int j = 0; j < 3; ++j) {
-          const double s2 = g->s[j] * g->s[j];
-          n0 += b[j] * a[j] / s2;
-          d0 += a[j] * a[j] / s2;
-        }
-        const double tau = n0 / d0;
-        if (!(tau > 0)) continue;
-        const double cth = 1.0 / xn; /* cos of the ray's angle to the optical axis */
-        /* lambda = sigma_x^2 tau(x)^2 with sigma_x^2 = sigma^2 cos^3(theta) / (fx fy), the
-         * pixel's area at unit distance along the ray */
-        const double lam = sig2 * cth * cth * cth * tau * tau;
-        double n1 = 0, d1 = 0, ratio = 1;
-        for (int j = 0; j < 3; ++j) {
-          const double s2 = g->s[j] * g->s[j], sh2 = s2 + lam;
-          n1 += b[j] * a[j] / sh2;
-          d1 += a[j] * a[j] / sh2;
-          ratio *= s2 / sh2;
-        }
-        const double tauh = n1 / d1;
-        if (!(tauh > 0)) continue;
-        D = 0; /* (tauh xh - mu)^T Sigma^_x^-1 (tauh xh - mu) */
-        for (int j = 0; j < 3; ++j) {
-          const double r = tauh * a[j] - b[j];
-          D += r * r / (g->s[j] * g->s[j] + lam);
-        }
-        /* modulation sqrt(|Sigma| x^T Sigma^-1 x / (|Sigma^_x| x^T Sigma^_x^-1 x)):
-         * ratio = |Sigma| / |Sigma^_x|, d0 = x^T Sigma^-1 x, d1 = x^T Sigma^_x^-1 x (unit x) */
-        mod = sqrt(ratio * d0 / d1);
-      } else if (gs_div) {
-        /* Sec. 3.1: (pi(x) - pi(mu))^T Sigma_pi^-1 (pi(x) - pi(mu)), pi(x) the pixel centre */
-        const double dx = (px + 0.5) - g->u[0], dy = (py + 0.5) - g->u[1];
-        D = g->A[0] * dx * dx + 2.0 * g->A[1] * dx * dy + g->A[2] * dy * dy;
-      } else {
-        double w[3];
-        for (int r = 0; r < 3; ++r) w[r] = g->W[3 * r] * x[0] + g->W[3 * r + 1] * x[1] + g->W[3 * r + 2] * x[2];
-        double num = g->m[0] * w[0] + g->m[1] * w[1] + g->m[2] * w[2]; /* x^T Si mu */
-        double den = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];          /* x^T Si x  */
-        double tau = num / den;
-        if (!(tau > 0)) continue;
-        double r0 = tau * w[0] - g->m[0], r1 = tau * w[1] - g->m[1], r2 = tau * w[2] - g->m[2];
-        D = r0 * r0 + r1 * r1 + r2 * r2;
-      }
-      double om = g->o * mod * exp(-0.5 * D);
+      double D, om;
+      if (!pixel_weight(g, x, px, py, mip_exact, gs_div, sig2, &D, &om)) continue;
       if (fabs(om - pmin) <= 1e-6) fl |= FLAG_CUTOFF;
       if (mip_exact ? !(om >= pmin) : !(D <= g->kappa)) continue;
       if (om > amax) om = amax;
@@ -576,8 +604,15 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
       ++cnt;
       h = (h ^ (uint64_t)(g->index + 1)) * 1099511628211ull;
     }
-    /* a primitive whose cull decision sits at its threshold may reach any pixel */
-    if (nb > 0) fl |= FLAG_BORDER;
+    /* a primitive whose skip decision sits within rounding of its threshold: the pixels it
+     * would reach (omega >= p_min / 2) */
+    for (int64_t k = 0; k < nb; ++k) {
+      double D, om;
+      if (pixel_weight(border[k], x, px, py, mip_exact, gs_div, sig2, &D, &om) && om >= 0.5 * pmin) {
+        fl |= FLAG_BORDER;
+        break;
+      }
+    }
     for (int ch = 0; ch < 3; ++ch) rgb[3 * p + ch] = C[ch];
     Tout[p] = T;
     if (ncontrib) ncontrib[p] = cnt;

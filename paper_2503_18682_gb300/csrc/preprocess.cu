@@ -11,7 +11,9 @@
 // For primitives whose scale ratio exceeds degenerate_ratio, the float32 result of a view
 // is replaced by the same stage run in FP64 (preprocess_fp64_kernel) when the float32
 // solve is ill-conditioned in that view (the disk is seen nearly edge-on), or for every
-// visible view when fp64_degenerate == 2.
+// visible view when fp64_degenerate == 2.  Independently of that setting, a pair whose
+// float32 skip decision (opacity below the cut-off, Eq. support; camera inside, Eq. c) lies
+// within the float32 rounding of its threshold is decided by the FP64 stage.
 #include "raygs_internal.cuh"
 #include "stage_math.cuh"
 
@@ -64,13 +66,27 @@ __device__ __forceinline__ bool tile_rect(bool full, float xmn, float xmx, float
   return true;
 }
 
+// Outcome of a vertex stage: the pair is skipped, kept, or (float32 only) one of its two
+// skip decisions -- kappa <= 0 (Eq. support) and c^2 <= kappa (Eq. c) -- lies within the
+// float32 rounding of its threshold, and the FP64 stage decides.
+enum StageResult { kSkip = 0, kKeep = 1, kUndecided = 2 };
+
+// Relative rounding bound of a float32 camera-frame projection R_c^T mu, as a fraction of
+// |mu|_1 (the float mean, the float rotation and the three-term dot product), with a
+// fourfold margin.
+constexpr float kProjErr32 = 2e-6f;
+
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
-// rotation; s: scales; o: prior opacity.  Returns false when the primitive is skipped or
-// covers no pixel of this view.
+// rotation; s: scales; o: prior opacity.  Returns kSkip when the primitive is skipped or
+// covers no pixel of this view.  With `decide` (float32 only), a skip decision within
+// rounding of its threshold returns kUndecided instead.
 template <typename T>
-__device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, const DevCam &cam,
-                           float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out,
-                           bool apply_mip = true) {
+__device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, const DevCam &cam,
+                          float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out,
+                          bool apply_mip = true, bool decide = true) {
+  const bool band = decide && sizeof(T) == 4;
+  const T mu1 = fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]);
+  T e_o = T(2e-6);  // relative rounding bound of o (the float32 sigmoid; grows with Eq. mip)
   // R_c = R_wc R_p: columns n_k are the primitive's axes in the camera frame.
   T Rc[9];
 #pragma unroll
@@ -90,26 +106,31 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
     // opacity is modulated by sqrt(|Sigma| c^2 / (|Sigma^| c^^2)).
     T lam = T(mip_sigma2) * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) /
             (T(cam.fx) * T(cam.fy));
-    T c2 = 0, c2h = 0, ratio = 1;
+    T c2 = 0, c2h = 0, ratio = 1, e2 = 0, e2h = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       T s2 = s[k] * s[k], s2h = s2 + lam;
       c2 += pk[k] * pk[k] / s2;
       c2h += pk[k] * pk[k] / s2h;
+      // rounding of c^2 and c^^2 through the projections pk
+      e2 += T(2) * fabs(pk[k]) * T(kProjErr32) * mu1 / s2;
+      e2h += T(2) * fabs(pk[k]) * T(kProjErr32) * mu1 / s2h;
       ratio *= s2 / s2h;
       s[k] = t_sqrt(s2h);
     }
     o *= t_sqrt(ratio * c2 / c2h);
+    e_o += T(0.5) * (e2 / c2 + e2h / c2h) + T(1e-6);
   }
   // Eq. support: kappa = -2 log(p_min / o); skip when kappa <= 0.
   T kappa = T(2) * t_log(o / T(p_min));
-  if (!(kappa > T(0))) return false;
+  if (band && fabs(kappa) <= T(2) * e_o + T(1e-6)) return kUndecided;
+  if (!(kappa > T(0))) return kSkip;
 
   // Conservative frustum test: every supported ray passes within sqrt(kappa) s_max of mu.
   {
     T smax = fmax(fmax(s[0], s[1]), s[2]);
     T rad = t_sqrt(kappa) * smax * T(1.001) + T(1e-6);
-    if (outside_frustum<T>(mu, rad, cam)) return false;
+    if (outside_frustum<T>(mu, rad, cam)) return kSkip;
   }
 
   // Sec. 3.2 Eq. c: c^2 = mu^T Sigma^-1 mu = |S^-1 R^T mu|^2; skip when c^2 <= kappa.
@@ -117,7 +138,15 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
 #pragma unroll
   for (int k = 0; k < 3; ++k) m[k] = pk[k] / s[k];
   T c2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-  if (!(c2 > kappa)) return false;
+  if (band) {
+    // each m_k carries the projection's rounding over s_k (large for thin primitives seen
+    // from near their plane), kappa that of log o
+    T e_c2 = T(1e-6) * (c2 + kappa) + T(2) * e_o;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e_c2 += T(2) * fabs(m[k]) * (T(kProjErr32) * mu1 / s[k] + T(1e-6) * fabs(m[k]));
+    if (fabs(c2 - kappa) <= e_c2) return kUndecided;
+  }
+  if (!(c2 > kappa)) return kSkip;
   T c = t_sqrt(c2);
 
   // ---- Sec. 4.1 quad.  mu^ = S^-1 R^T mu / c; R_{mu^<-v} of App. A.1 (columns 0, 1).
@@ -231,7 +260,7 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
       }
     }
   }
-  return tile_rect(full, xmn, xmx, ymn, ymx, cam, tile_w, tile_h, out);
+  return tile_rect(full, xmn, xmx, ymn, ymx, cam, tile_w, tile_h, out) ? kKeep : kSkip;
 }
 
 // GS vertex stage (Sec. 3.1) in precision T: Sigma_pi = J Sigma J^T with J the Jacobian of
@@ -246,10 +275,11 @@ __device__ bool view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, c
 // and its exponent D_gs log2(e) / 2.  The support is the ellipse delta^T A delta <= kappa.
 // There is no camera-inside skip (Eq. c) and no Eq. mip term.
 template <typename T>
-__device__ bool gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
-                              int tile_w, int tile_h, StageOut &out) {
+__device__ int gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
+                             int tile_w, int tile_h, StageOut &out) {
   T kappa = T(2) * t_log(o / T(p_min));
-  if (!(kappa > T(0))) return false;
+  if (sizeof(T) == 4 && fabs(kappa) <= T(5e-6)) return kUndecided;  // o within rounding of p_min
+  if (!(kappa > T(0))) return kSkip;
   T Rc[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -278,7 +308,7 @@ __device__ bool gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, c
   }
   const T sd = s[0] * s[1] * s[2] * jx * jy * iz;
   const T det = sd * sd * c2;  // det Sigma_pi
-  if (!(det > T(0)) || !(P00 > T(0)) || !(P11 > T(0))) return false;
+  if (!(det > T(0)) || !(P00 > T(0)) || !(P11 > T(0))) return kSkip;
   // A = Sigma_pi^-1 = [[P11, -P01], [-P01, P00]] / det; G00 = sqrt(A00), G01 = A01 / G00,
   // G11 = sqrt(det A) / G00 with det A = 1 / det Sigma_pi
   const T idet = T(1) / det;
@@ -303,7 +333,9 @@ __device__ bool gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, c
   const T ucx = jx * mu[0] + T(cam.cx), ucy = jy * mu[1] + T(cam.cy);
   const T hx = t_sqrt(kappa * T(1.001) * P00), hy = t_sqrt(kappa * T(1.001) * P11);
   return tile_rect(false, float(ucx - hx), float(ucx + hx), float(ucy - hy), float(ucy + hy), cam, tile_w,
-                   tile_h, out);
+                   tile_h, out)
+             ? kKeep
+             : kSkip;
 }
 
 // Per-pixel constants of the exact anti-aliasing (Sec. 5, pixel-dependent form), in the
@@ -332,10 +364,12 @@ struct MipxOut {
 // sigma_x^2), and D^(x) >= D(x; Sigma + Lambda I) for lambda(x) <= Lambda.  When k >= 1/2, or
 // when the inflated support reaches the camera, the pair covers its whole view.
 template <typename T>
-__device__ bool mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
-                                float mip_sigma2, int tile_w, int tile_h, StageOut &out, MipxOut &X) {
+__device__ int mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam, float p_min,
+                               float mip_sigma2, int tile_w, int tile_h, StageOut &out, MipxOut &X) {
+  const bool band = sizeof(T) == 4;
   const T kappa = T(2) * t_log(o / T(p_min));
-  if (!(kappa > T(0))) return false;
+  if (band && fabs(kappa) <= T(5e-6)) return kUndecided;  // o within rounding of p_min
+  if (!(kappa > T(0))) return kSkip;
   T Rc[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -350,7 +384,14 @@ __device__ bool mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o,
     mt[k] = pk[k] / s[k];
   }
   const T c2 = mt[0] * mt[0] + mt[1] * mt[1] + mt[2] * mt[2];
-  if (!(c2 > kappa)) return false;  // Eq. c on the plain primitive
+  if (band) {  // Eq. c within rounding of its threshold (see view_stage)
+    const T mu1 = fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]);
+    T e_c2 = T(1e-6) * (c2 + kappa) + T(5e-6);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e_c2 += T(2) * fabs(mt[k]) * (T(kProjErr32) * mu1 / s[k] + T(1e-6) * fabs(mt[k]));
+    if (fabs(c2 - kappa) <= e_c2) return kUndecided;
+  }
+  if (!(c2 > kappa)) return kSkip;  // Eq. c on the plain primitive
   const T smax = fmax(fmax(s[0], s[1]), s[2]), smin = fmin(fmin(s[0], s[1]), s[2]);
   const T sa2 = T(mip_sigma2) / (T(cam.fx) * T(cam.fy));
   const T kk = t_sqrt(kappa) * t_sqrt(sa2) * (T(1) + smax / smin);
@@ -368,7 +409,7 @@ __device__ bool mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o,
     }
     if (c2I > kappa * T(1.001)) {
       full = false;
-      if (!view_stage<T>(mu, Rp, sI, o, cam, p_min, 0.f, tile_w, tile_h, out, false)) return false;
+      if (view_stage<T>(mu, Rp, sI, o, cam, p_min, 0.f, tile_w, tile_h, out, false, false) != kKeep) return kSkip;
       if (!(out.M00 > 0.f)) out.M00 = -2.f;  // not a bounded ellipse: whole rectangle rows
     }
   }
@@ -392,7 +433,7 @@ __device__ bool mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o,
   }
   X.kappa = float(kappa);
   out.lo2o = float(t_log(o) * T(1.4426950408889634));
-  return true;
+  return kKeep;
 }
 
 __device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t idx, const DevCam &cam,
@@ -463,7 +504,7 @@ constexpr int kViewChunk = 16;
 enum StageMode { kStageRay = 0, kStageGS = 1, kStageExact = 2 };
 
 template <int MODE, typename T>
-__device__ __forceinline__ bool stage_for(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam,
+__device__ __forceinline__ int stage_for(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam,
                                           const PrepParams &P, StageOut &so, MipxOut &mx) {
   if (MODE == kStageGS) return gs_view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.tile_w, P.tile_h, so);
   if (MODE == kStageExact)
@@ -536,7 +577,9 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       const float kappa0 = 2.f * logf(o / P.p_min);
       const float smax = fmaxf(fmaxf(s0, s1), s2);
       s_s2max[t] = smax * smax;
-      s_rad[t] = kappa0 > 0.f ? sqrtf(kappa0) : -1.f;  // < 0: culled everywhere
+      // < 0: culled everywhere; an opacity within rounding of p_min goes on to the full
+      // stage, which leaves the decision to the FP64 stage
+      s_rad[t] = kappa0 > 0.f ? sqrtf(kappa0) : (kappa0 >= -1e-5f ? 4e-3f : -1.f);
     }
   }
 
@@ -595,8 +638,10 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       for (int k = 0; k < 9; ++k) Rp[k] = s_R[9 * tt + k];
       StageOut so;
       MipxOut mxo;
-      if (!stage_for<MODE, float>(mu, Rp, sv, s_o[tt], cam, P, so, mxo)) {
+      const int res = stage_for<MODE, float>(mu, Rp, sv, s_o[tt], cam, P, so, mxo);
+      if (res != kKeep) {
         P.depth_key[idx] = kCulled;
+        if (res == kUndecided) P.deg_list[atomicAdd(P.deg_count, 1u)] = uint32_t(idx);
         continue;
       }
       const float dx = mx - cam.C[0], dy = my - cam.C[1], dz = mz - cam.C[2];
@@ -642,7 +687,7 @@ __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
                           double(muc[2].hi) + double(muc[2].lo)};
     StageOut so;
     MipxOut mxo;
-    if (!stage_for<MODE, double>(mu, Rp, s, o, cam, P, so, mxo)) {
+    if (stage_for<MODE, double>(mu, Rp, s, o, cam, P, so, mxo) != kKeep) {
       P.depth_key[idx] = kCulled;
       continue;
     }
@@ -679,7 +724,7 @@ cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st)
 #undef RAYGS_PREP
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (P.fp64_degenerate) {
+  {  // the listed pairs: near-degenerate ones and undecided skip decisions
     int gb = num_sms * 4;
 #define RAYGS_FP64(D, M) preprocess_fp64_kernel<D, M><<<gb, 128, 0, st>>>(P)
 #define RAYGS_FP64_MODES(D)                 \

@@ -1,7 +1,8 @@
 """Forward parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
 element, on seeded scenes that span several tiles and ragged image edges; plus edge cases.
 Tolerance: 2e-4 max-abs per channel (and on T), excluding at most 0.01% of pixels, each of
-which the oracle flags as sitting at a cut-off / stop decision boundary."""
+which the oracle flags as sitting at the opacity cut-off (or reached by a primitive whose skip
+decision lies within FP64 rounding of its threshold)."""
 import numpy as np
 import pytest
 

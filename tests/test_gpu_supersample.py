@@ -48,7 +48,7 @@ def test_supersampled_views_match_oracle_sub_pixel_mean(oracle_lib):
         orc = oracle_lib.render(scene, ch)
         o_rgb = orc["rgb"].reshape(h, f, w, f, 3).mean(axis=(1, 3)).reshape(-1, 3)
         o_T = orc["T"].reshape(h, f, w, f).mean(axis=(1, 3)).reshape(-1)
-        o_flag = orc["flags"].reshape(h, f, w, f).max(axis=(1, 3)).reshape(-1)
+        o_flag = np.bitwise_or.reduce(orc["flags"].reshape(h, f, w, f), axis=(1, 3)).reshape(-1)
         st = compare(rgb[base:base + w * h], T[base:base + w * h], dict(rgb=o_rgb, T=o_T, flags=o_flag))
         assert st["n_unexplained"] == 0 and st["max_err"] <= TOL and st["max_err_T"] <= TOL, st
         base += w * h
