@@ -10,8 +10,6 @@
 //
 // The array is a module-scope __device__ variable: every GPU that loads this library keeps
 // kNoAllocScratchBytes of device memory reserved for it until the process exits.
-#include <mutex>
-
 #include "raygs_internal.cuh"
 
 namespace raygs {
@@ -25,26 +23,19 @@ using namespace raygs;
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  Host code cannot use the
-// symbol itself (it names a host-side shadow); the address is looked up once per device
-// with that device current, which also loads the module on that device.
+// Device address of the scratch array in the current device's context.  Host code cannot
+// use the symbol itself (it names a host-side shadow).  The lookup is made on every call:
+// it is cheap once the module is loaded, and it stays right if the context was destroyed
+// and created again (cudaDeviceReset), where the array may sit at a new address.  The
+// first call on a device loads the module there.
 raygs_status scratch_for_current_device(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { note_cuda_error(e); return RAYGS_ERR_CUDA; }
-  if (dev < 0 || dev >= kMaxDevices) return RAYGS_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) { note_cuda_error(e); return RAYGS_ERR_CUDA; }
-    g_scratch_ptr[dev] = p;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    note_cuda_error(e);
+    return RAYGS_ERR_CUDA;
   }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return RAYGS_OK;
 }
 
@@ -74,8 +65,12 @@ extern "C" raygs_status raygs_render_noalloc(const raygs_camera *cams, int32_t n
   s = scratch_for_current_device(&scratch);
   if (s != RAYGS_OK) return s;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  cudaError_t ae = cudaGetDevice(&dev);
+  if (ae == cudaSuccess) ae = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ae != cudaSuccess || sms <= 0) {
+    note_cuda_error(ae);
+    return RAYGS_ERR_CUDA;
+  }
 
   // Size check: the fixed part must fit; the rest of the array bounds the tile rows and
   // instances (kBytesPerCapacity bytes per unit of capacity).

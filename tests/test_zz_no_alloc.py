@@ -88,3 +88,31 @@ def test_noalloc_gs_divergence_and_exact_refusal(rg):
     status = rg.raygs_render_noalloc([dict(cams[0], mip="exact")], rg.make_scene(st), None, rgb, T, nc,
                                      check=False)
     assert status == 1  # RAYGS_ERR_INVALID_ARG
+
+
+def test_noalloc_instance_overflow_then_normal_call(rg):
+    """Few large primitives over a 1920x1080 view emit far more (primitive, tile) instances
+    than the array's remaining space holds: the call renders what fits and reports
+    RAYGS_ERR_CAPACITY.  The next call on a small scene is unaffected (same image as the
+    plan path)."""
+    import torch
+    big = scenes.uniform_scene(5000, seed=34)
+    big["log_scales"][:] = np.float32(np.log(0.5))
+    cams = [scenes.make_camera(1920, 1080, 1000.0, 1000.0)]
+    st = rg.scene_to_device(big)
+    rgb, T, nc = _outputs(torch, 1920 * 1080)
+    status = rg.raygs_render_noalloc(cams, rg.make_scene(st), None, rgb, T, nc, check=False)
+    assert status == 2, rg.lib().raygs_status_string(status)  # RAYGS_ERR_CAPACITY after the render
+    torch.cuda.synchronize()
+    scene = scenes.uniform_scene(2000, seed=31)
+    cams = [scenes.make_camera(64, 64, 64.0, 64.0, 32.0, 32.0)]
+    st = rg.scene_to_device(scene)
+    ref = rg.Renderer(cams, 2000)
+    rgb0, T0, nc0 = ref.forward(st)
+    torch.cuda.synchronize()
+    rgb, T, nc = _outputs(torch, ref.num_pixels)
+    status = rg.raygs_render_noalloc(cams, rg.make_scene(st), None, rgb, T, nc, check=False)
+    assert status == 0, rg.lib().raygs_status_string(status)
+    torch.cuda.synchronize()
+    assert float((rgb - rgb0).abs().max()) <= TOL and float((T - T0).abs().max()) <= TOL
+    assert torch.equal(nc, nc0)
