@@ -295,7 +295,8 @@ def run_ours(args, world, rank, local):
         sc = raygs.make_scene(st)
         r.forward(st, rgb, T, nc, stream=stream)
         ctr = dict(r.last_counters)
-        evals, comps = r.counted_render(rgb, T, nc, stream=stream)
+        rstat = r.counted_render_stats(rgb, T, nc, stream=stream)
+        evals, comps = rstat["evaluated"], rstat["composited"]
         raygs.raygs_graph_capture(r.plan, sc, rgb, T, nc, stream)
     stream.synchronize()
 
@@ -428,6 +429,11 @@ def run_ours(args, world, rank, local):
         composited_pairs_per_s=comps / (stages["render_ms"] * 1e-3),
         evaluated_pairs=evals, composited_pairs=comps,
         n_visible=ctr["n_visible"], n_instances=ctr["n_instances"],
+        raster_work=dict(consumed_instances=rstat["consumed"],
+                         consumed_frac=rstat["consumed"] / max(1, ctr["n_instances"]),
+                         thread_record_iterations=rstat["iterations"],
+                         live_pixels_per_iteration=evals / max(1, rstat["iterations"]),
+                         composited_per_evaluated=comps / max(1, evals)),
         stages=dict(stages, preprocess_hbm_gbs=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9,
                     preprocess_hbm_frac=prep_bytes / (stages["preprocess_ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
                     bin_sort_bytes=bin_bytes,

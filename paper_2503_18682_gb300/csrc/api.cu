@@ -281,14 +281,16 @@ raygs_status raygs_render_backward(raygs_plan *plan, const raygs_scene *scene, c
 }
 
 /* ------------------------------------------------------------------ diagnostics
- * Not part of the documented ABI: an instrumented render that also counts evaluated and
- * composited (pixel, primitive) pairs, and raw access to the binning buffers for tests. */
+ * Not part of the documented ABI: an instrumented render that also counts, into
+ * host_counts[0..3], evaluated and composited (pixel, primitive) pairs, the list entries the
+ * rasteriser staged before its tiles stopped (consumed instances) and its (thread, record)
+ * iterations; and raw access to the binning buffers for tests. */
 raygs_status raygs_debug_render_counted(raygs_plan *plan, float *rgb, float *T_final, int32_t *n_contrib,
                                         unsigned long long *host_counts, void *stream) {
   raygs_status s = render_impl(plan, rgb, T_final, n_contrib, true, stream);
   if (s != RAYGS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(host_counts, plan->w.base + plan->w.L.evals, 2 * sizeof(unsigned long long),
+  cudaError_t e = cudaMemcpyAsync(host_counts, plan->w.base + plan->w.L.evals, 4 * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
@@ -301,7 +303,8 @@ raygs_status raygs_debug_render_counted(raygs_plan *plan, float *rgb, float *T_f
  *        3 sorted pair ids [n_visible], 4 support rows sorted by tile row [n_rows_kept]
  *        (uint2: sorted pair position, first tile column | run length << 16),
  *        5 instance lists (sorted pair positions, tile by tile), 6 tile ranges [tiles] (uint2),
- *        7 support ellipses [V*N] (32 B), 8 raw counters */
+ *        7 support ellipses [V*N] (32 B), 8 raw counters, 9 per-tile stop positions of the
+ *        last instrumented render [tiles] (kCulled: the list ran out first) */
 void *raygs_debug_buffer(raygs_plan *plan, int which) {
   if (!plan || !plan->w.base) return nullptr;
   const Work &w = plan->w;
@@ -315,6 +318,7 @@ void *raygs_debug_buffer(raygs_plan *plan, int which) {
     case 6: return w.base + w.L.ranges;
     case 7: return w.base + w.L.ell;
     case 8: return w.base + w.L.counters;
+    case 9: return w.base + w.L.tstop;
   }
   return nullptr;
 }

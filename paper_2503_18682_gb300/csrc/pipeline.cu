@@ -85,7 +85,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   const size_t C = size_t(cap);
   L.cams = take(sizeof(DevCam) * size_t(n_views));
   L.counters = take(sizeof(Counters));
-  L.evals = take(2 * sizeof(unsigned long long));
+  L.evals = take(4 * sizeof(unsigned long long));
   L.tilectr = take(16);
   L.tscan = take(2 * sizeof(unsigned long long));
   L.depth = take(4 * VN);
@@ -112,6 +112,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.ccnt = take(4 * size_t(max_chunks) * size_t(max_tiles_x > 0 ? max_tiles_x : 1) + 16);
   L.hist = take(4 * 512 * size_t(G) + 4 * (512 * size_t(G) / 2048 + 1));
   L.ranges = take(8 * size_t(tiles));
+  L.tstop = take(4 * size_t(tiles) + 16);
   L.deg = take(4 * VN);
   L.degc = take(4);
   L.partials = backward ? take(4 * kGradW * C + 16) : 0;
@@ -324,8 +325,9 @@ cudaError_t run_render(const Work &w, float *rgb, float *T_final, int32_t *n_con
   P.Tf = T_final;
   P.ncontrib = n_contrib;
   P.eval_counts = w.at<unsigned long long>(w.L.evals);
+  P.tile_stop = count ? w.at<uint32_t>(w.L.tstop) : nullptr;
   if (count) {
-    cudaError_t e = cudaMemsetAsync(P.eval_counts, 0, 2 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(P.eval_counts, 0, 4 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
   if (P.recx) return launch_render_mipx(P, w.cfg.tile_w, w.cfg.tile_h, w.tiles, count, st);

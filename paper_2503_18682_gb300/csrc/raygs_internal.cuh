@@ -264,7 +264,11 @@ struct RenderParams {
   float *rgb;
   float *Tf;
   int *ncontrib;
-  unsigned long long *eval_counts;  // [2]: evaluated and composited (pixel, primitive) pairs
+  // [4]: evaluated and composited (pixel, primitive) pairs, list entries the CTAs staged
+  // (consumed instances), (thread, record) iterations with a live pixel
+  unsigned long long *eval_counts;
+  uint32_t *tile_stop;  // instrumented variant: per tile, list entries staged before every pixel
+                        // stopped, or kCulled when the list ran out first (nullable)
 };
 
 constexpr int kEmitTile = 2048;
@@ -340,7 +344,7 @@ cudaError_t launch_resolve(const float *rgb_hi, const float *T_hi, float *rgb_lo
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t tilectr, cams, counters, evals, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
+  size_t tilectr, cams, counters, evals, tstop, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
       seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, cbase, ccnt, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
     if (py < cam.H && px + k * QX < cam.W) alive |= 1u << k;
   }
   const uint32_t inside = alive;
-  unsigned long long n_eval = 0, n_comp = 0;
+  unsigned long long n_eval = 0, n_comp = 0, n_iter = 0;
+  uint32_t stop_at = rg.y;  // first list entry the CTA did not stage
 
   // Records move through a two-stage pipeline: while a batch is composited, the raw
   // records of the next batch are in flight to shared memory (cp.async) and the record
@@ -84,7 +85,10 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
   }
 
   for (uint32_t start = rg.x; start < rg.y; start += NB) {
-    if (__syncthreads_and(alive == 0)) break;
+    if (__syncthreads_and(alive == 0)) {
+      stop_at = start;
+      break;
+    }
     cp_async_wait_all();  // this thread's raw slots of the batch have landed
 #pragma unroll
     for (int rr = 0; rr < PER; ++rr) {
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
     for (int j = 0; j < nb && alive; ++j) {
       const float4 A = s_A[j], B = s_B[j];
       const float4 Cc = s_C[j];
-      if (COUNT) n_eval += __popc(alive);
+      if (COUNT) { n_eval += __popc(alive); ++n_iter; }
       // with 8 pixels per thread a conservative segment test pays for itself (fewer
       // pixels per thread are cheaper to test directly); the instrumented variant tests
       // every pixel, so its image checks the filter
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
     }
   }
   cp_async_wait_all();  // no copy may outlive the block
+  const bool alive_any = COUNT ? __syncthreads_or(alive != 0) : false;
   if (inside) {
     const long long pix = cam.pix_base + (long long)py * cam.W + px;
 #pragma unroll
@@ -162,10 +167,16 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
     for (int o = 16; o > 0; o >>= 1) {
       n_eval += __shfl_down_sync(0xffffffffu, n_eval, o);
       n_comp += __shfl_down_sync(0xffffffffu, n_comp, o);
+      n_iter += __shfl_down_sync(0xffffffffu, n_iter, o);
     }
     if ((tid & 31) == 0) {
       atomicAdd(&P.eval_counts[0], n_eval);
       atomicAdd(&P.eval_counts[1], n_comp);
+      atomicAdd(&P.eval_counts[3], n_iter);
+    }
+    if (tid == 0) {
+      atomicAdd(&P.eval_counts[2], (unsigned long long)(stop_at - rg.x));
+      if (P.tile_stop) P.tile_stop[tile] = alive_any ? kCulled : stop_at - rg.x;
     }
   }
   __syncthreads();  // shared state and s_tile are free before the next claim

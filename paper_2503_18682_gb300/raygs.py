@@ -452,12 +452,20 @@ class Renderer:
 
     def counted_render(self, rgb, T=None, nc=None, stream=None):
         """Instrumented render: returns (evaluated pairs, composited pairs)."""
-        out = (C.c_ulonglong * 2)()
+        st = self.counted_render_stats(rgb, T, nc, stream)
+        return st["evaluated"], st["composited"]
+
+    def counted_render_stats(self, rgb, T=None, nc=None, stream=None) -> dict:
+        """Instrumented render: evaluated and composited (pixel, primitive) pairs, consumed
+        list entries (records the tiles staged before they stopped) and the rasteriser's
+        (thread, record) iterations."""
+        out = (C.c_ulonglong * 4)()
         _check(lib().raygs_debug_render_counted(self.plan, rgb.data_ptr(),
                                                 T.data_ptr() if T is not None else None,
                                                 nc.data_ptr() if nc is not None else None,
                                                 out, stream_ptr(stream)), "raygs_debug_render_counted")
-        return int(out[0]), int(out[1])
+        return dict(evaluated=int(out[0]), composited=int(out[1]), consumed=int(out[2]),
+                    iterations=int(out[3]))
 
     def debug_buffer(self, which: int) -> int:
         return int(lib().raygs_debug_buffer(self.plan, which) or 0)
