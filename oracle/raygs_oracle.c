@@ -35,7 +35,7 @@
  *   - Rendering equation (Sec. 3, Eq. rendering): front-to-back compositing over the
  *     primitives in ascending order of their centre's depth.
  *
- * Readings taken where the paper is silent (each one is listed in the design notes):
+ * Readings taken where the paper is silent:
  *   - only rays with tau > 0 count (the density maximum lies in front of the camera);
  *   - the near plane culls whole primitives (Sec. 4.1, "near plane clipping");
  *   - omega is clamped to alpha_max (0.99) and compositing stops before a primitive that

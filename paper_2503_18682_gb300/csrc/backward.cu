@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
     for (int slot = tid; slot < nb; slot += NT) {
       const uint32_t pos = P.inst_vals[rg.x + start + slot];
       const Rec r = P.rec[P.pairs[pos]];
-      stage_record(r, ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
+      stage_record<0>(r, ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
       s_e[slot] = emission_index(P, pos, ty, tx);
     }
     for (int i = tid; i < nb * kGradW; i += NT) (&s_acc[0][0])[i] = 0.f;
@@ -129,18 +129,20 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       const float4 Cs = s_C[j];
       // as in the forward pass, the segment filter pays only at 8 pixels per thread
       const uint32_t hit = (PX < 8 || row_may_hit<PX>(A, B, Cs, s_D[j].w, fl_x, fl_y, step))
-                               ? eval_pixels<PX>(A, B, Cs.x, fl_x, fl_y, step, q, r, y0, y1, y2)
+                               ? eval_pixels<PX>(A, B, fl_x, fl_y, step, q, r, y0, y1, y2)
                                : 0u;
       float acc[kGradW];
 #pragma unroll
       for (int c = 0; c < kGradW; ++c) acc[c] = 0.f;
       bool any = false;
+      // the staged G carries sqrt(kp): y01 = y01' / sqrt(kp), q = q' / kp
+      const float ikp = hit ? 1.f / Cs.x : 0.f, isk = hit ? sqrtf(ikp) : 0.f;
 #pragma unroll
       for (int k = 0; k < PX; ++k) {
         if ((hit & (1u << k)) && pos < last[k]) {
           any = true;
           const float4 Cc = s_C[j], Dd = s_D[j];
-          const float raw = pixel_opacity(Cc, q[k], r[k], 1.f);
+          const float raw = pixel_opacity<0>(Cc, q[k], r[k]);
           const bool clamped = raw > P.alpha_max;
           const float om = clamped ? P.alpha_max : raw;
           const float onem = 1.f - om;
@@ -159,8 +161,9 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
           if (!clamped) {
             const float dLdD = -0.5f * om * dLdw;
             acc[9] += dLdw * om;
-            const float inv = sqrtf(Cc.y * (2.f / kLog2e)) / (q[k] + r[k]);
-            const float rho0 = y2[k] * y0[k] * inv, rho1 = y2[k] * y1[k] * inv, rho2 = -q[k] * inv;
+            const float qu = q[k] * ikp;
+            const float inv = sqrtf(Cc.y * (2.f / kLog2e)) / (qu + r[k]);
+            const float rho0 = y2[k] * (y0[k] * isk) * inv, rho1 = y2[k] * (y1[k] * isk) * inv, rho2 = -qu * inv;
             acc[0] += dLdD * rho0;
             acc[1] += dLdD * rho1;
             acc[2] += dLdD * rho2;

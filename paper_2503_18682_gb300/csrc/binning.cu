@@ -450,14 +450,15 @@ __device__ __forceinline__ bool ellipse_band(const Ell &e, float ya, float yb, f
 // bisection with a vertical-line test.
 
 // Does the segment delta(t) = P + t E, t in [0, 1] (pixel offsets from the projected
-// centre) meet the support kp |G delta|^2 <= y2^2, y2 = 1 + h.delta > 0?  Along the
-// segment y01 = a + t b and y2 = al + t be, so f = kp |y01|^2 - y2^2 is a quadratic in t;
+// centre) meet the support |G delta|^2 <= y2^2, y2 = 1 + h.delta > 0 (the record's G carries
+// sqrt(kp))?  Along the segment y01' = a + t b and y2 = al + t be, so f = |y01'|^2 - y2^2 is a
+// quadratic in t;
 // its minimum over the part where y2 > 0 is compared with a margin of 1e-4 of the
 // magnitude of its terms, far above float32 rounding: the answer errs only towards yes.
 // t_at receives the parameter of that minimum.
 __device__ __forceinline__ bool segment_meets_support(const Rec &r, float Px, float Py, float Ex, float Ey,
                                                       float *t_at = nullptr) {
-  const float kp = r.c.z;
+  const float kp = 1.f;
   const float a0 = fmaf(r.b.x, Px, r.b.y * Py), a1 = fmaf(r.b.z, Px, r.b.w * Py);
   const float b0 = fmaf(r.b.x, Ex, r.b.y * Ey), b1 = fmaf(r.b.z, Ex, r.b.w * Ey);
   const float al = fmaf(r.c.x, Px, fmaf(r.c.y, Py, 1.f)), be = fmaf(r.c.x, Ex, r.c.y * Ey);

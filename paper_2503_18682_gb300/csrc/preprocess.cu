@@ -76,6 +76,65 @@ enum StageResult { kSkip = 0, kKeep = 1, kUndecided = 2 };
 // fourfold margin.
 constexpr float kProjErr32 = 2e-6f;
 
+// Sec. 4.1 vertex stage: the smallest enclosing quad V_ray (App. A.1-A.3) of the
+// primitive's support in the camera frame and the screen bounding box of its projected
+// vertices; full = true when a vertex lies behind the camera plane (the box is then the
+// whole view).  m = S^-1 R_c^T mu, c = |m|.
+template <typename T>
+__device__ __forceinline__ void quad_screen_box(const T mu[3], const T Rc[9], const T s[3], const T m[3], T c, T c2,
+                                                T kappa, const DevCam &cam, bool &full, float &xmn, float &xmx,
+                                                float &ymn, float &ymx) {
+  // mu^ = S^-1 R^T mu / c; R_{mu^<-v} of App. A.1 (columns 0, 1).
+  T mh0 = m[0] / c, mh1 = m[1] / c, mh2 = m[2] / c;
+  bool up = mh2 >= T(0);
+  T a0 = mh0, a1 = mh1, a2 = up ? mh2 + T(1) : mh2 - T(1);
+  T inv = T(2) / (a0 * a0 + a1 * a1 + a2 * a2);
+  T r0[3] = {inv * a0 * a0 - T(1), inv * a1 * a0, inv * a2 * a0};
+  T r1[3] = {inv * a0 * a1, inv * a1 * a1 - T(1), inv * a2 * a1};
+  if (!up) { r0[0] = -r0[0]; r0[1] = -r0[1]; r0[2] = -r0[2]; }  // times P = diag(-1,1,-1)
+  // Q_{0:2} = R S R_{mu^<-v} restricted to its first two columns (Eq. invPhi).
+  T q0[3], q1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    q0[i] = Rc[3 * i] * s[0] * r0[0] + Rc[3 * i + 1] * s[1] * r0[1] + Rc[3 * i + 2] * s[2] * r0[2];
+    q1[i] = Rc[3 * i] * s[0] * r1[0] + Rc[3 * i + 1] * s[1] * r1[1] + Rc[3 * i + 2] * s[2] * r1[2];
+  }
+  // Eq. optim2: u1 = top eigenvector of B = Q_{0:2}^T Q_{0:2} (half-angle form).
+  T B00 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+  T B01 = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2];
+  T B11 = q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2];
+  T dd = B00 - B11, rho = t_sqrt(dd * dd + T(4) * B01 * B01);
+  T u1x = T(1), u1y = T(0);
+  if (rho > T(1e-12) * (B00 + B11)) {
+    if (dd >= T(0)) { u1x = dd + rho; u1y = T(2) * B01; }
+    else { u1x = T(2) * B01; u1y = rho - dd; }
+    T un = T(1) / t_sqrt(u1x * u1x + u1y * u1y);
+    u1x *= un; u1y *= un;
+  }
+  // u0 = u1 rotated by +90 degrees; Z_ray = (sqrt(kappa)/b) O, b = sqrt(1 - kappa/c^2).
+  T zs = t_sqrt(kappa) / t_sqrt(T(1) - kappa / c2);
+  T A0[3], A1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    A0[i] = zs * (-u1y * q0[i] + u1x * q1[i]);  // Q_{0:2} u0
+    A1[i] = zs * (u1x * q0[i] + u1y * q1[i]);   // Q_{0:2} u1
+  }
+  // Eq. V_ray: vertices mu + (+-1) A0 + (+-1) A1; screen bounding box of their projections.
+  full = false;
+  xmn = 3.0e38f; xmx = -3.0e38f; ymn = 3.0e38f; ymx = -3.0e38f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T sa = (k & 2) ? T(1) : T(-1), sb = (k == 1 || k == 2) ? T(1) : T(-1);
+    T px = mu[0] + sa * A0[0] + sb * A1[0];
+    T py = mu[1] + sa * A0[1] + sb * A1[1];
+    T pz = mu[2] + sa * A0[2] + sb * A1[2];
+    if (!(pz > T(1e-12))) { full = true; continue; }
+    float u = float(T(cam.fx) * px / pz + T(cam.cx));
+    float v = float(T(cam.fy) * py / pz + T(cam.cy));
+    xmn = fminf(xmn, u); xmx = fmaxf(xmx, u); ymn = fminf(ymn, v); ymx = fmaxf(ymx, v);
+  }
+}
+
 // The per-(primitive, view) stage in precision T.  mu: camera-frame mean; Rp: world-frame
 // rotation; s: scales; o: prior opacity.  Returns kSkip when the primitive is skipped or
 // covers no pixel of this view.  With `decide` (float32 only), a skip decision within
@@ -149,55 +208,9 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
   if (!(c2 > kappa)) return kSkip;
   T c = t_sqrt(c2);
 
-  // ---- Sec. 4.1 quad.  mu^ = S^-1 R^T mu / c; R_{mu^<-v} of App. A.1 (columns 0, 1).
-  T mh0 = m[0] / c, mh1 = m[1] / c, mh2 = m[2] / c;
-  bool up = mh2 >= T(0);
-  T a0 = mh0, a1 = mh1, a2 = up ? mh2 + T(1) : mh2 - T(1);
-  T inv = T(2) / (a0 * a0 + a1 * a1 + a2 * a2);
-  T r0[3] = {inv * a0 * a0 - T(1), inv * a1 * a0, inv * a2 * a0};
-  T r1[3] = {inv * a0 * a1, inv * a1 * a1 - T(1), inv * a2 * a1};
-  if (!up) { r0[0] = -r0[0]; r0[1] = -r0[1]; r0[2] = -r0[2]; }  // times P = diag(-1,1,-1)
-  // Q_{0:2} = R S R_{mu^<-v} restricted to its first two columns (Eq. invPhi).
-  T q0[3], q1[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    q0[i] = Rc[3 * i] * s[0] * r0[0] + Rc[3 * i + 1] * s[1] * r0[1] + Rc[3 * i + 2] * s[2] * r0[2];
-    q1[i] = Rc[3 * i] * s[0] * r1[0] + Rc[3 * i + 1] * s[1] * r1[1] + Rc[3 * i + 2] * s[2] * r1[2];
-  }
-  // Eq. optim2: u1 = top eigenvector of B = Q_{0:2}^T Q_{0:2} (half-angle form).
-  T B00 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
-  T B01 = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2];
-  T B11 = q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2];
-  T dd = B00 - B11, rho = t_sqrt(dd * dd + T(4) * B01 * B01);
-  T u1x = T(1), u1y = T(0);
-  if (rho > T(1e-12) * (B00 + B11)) {
-    if (dd >= T(0)) { u1x = dd + rho; u1y = T(2) * B01; }
-    else { u1x = T(2) * B01; u1y = rho - dd; }
-    T un = T(1) / t_sqrt(u1x * u1x + u1y * u1y);
-    u1x *= un; u1y *= un;
-  }
-  // u0 = u1 rotated by +90 degrees; Z_ray = (sqrt(kappa)/b) O, b = sqrt(1 - kappa/c^2).
-  T zs = t_sqrt(kappa) / t_sqrt(T(1) - kappa / c2);
-  T A0[3], A1[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    A0[i] = zs * (-u1y * q0[i] + u1x * q1[i]);  // Q_{0:2} u0
-    A1[i] = zs * (u1x * q0[i] + u1y * q1[i]);   // Q_{0:2} u1
-  }
-  // Eq. V_ray: vertices mu + (+-1) A0 + (+-1) A1; screen bounding box of their projections.
   bool full = false;
   float xmn = 3.0e38f, xmx = -3.0e38f, ymn = 3.0e38f, ymx = -3.0e38f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    T sa = (k & 2) ? T(1) : T(-1), sb = (k == 1 || k == 2) ? T(1) : T(-1);
-    T px = mu[0] + sa * A0[0] + sb * A1[0];
-    T py = mu[1] + sa * A0[1] + sb * A1[1];
-    T pz = mu[2] + sa * A0[2] + sb * A1[2];
-    if (!(pz > T(1e-12))) { full = true; continue; }
-    float u = float(T(cam.fx) * px / pz + T(cam.cx));
-    float v = float(T(cam.fy) * py / pz + T(cam.cy));
-    xmn = fminf(xmn, u); xmx = fmaxf(xmx, u); ymn = fminf(ymn, v); ymx = fmaxf(ymx, v);
-  }
+
   // ---- Per-pixel factors.  With y = K x, K = Q^-1 (App. A.4 steps g-i),
   // D = c^2 |y01|^2 / |y|^2, which is the fragment formula 1/(c^-2 + |Z a|^-2) with the
   // quad coordinate Z a = c U^T y01 / y2 read off the pixel ray.  The rows of K01 span the
@@ -207,10 +220,13 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
   T k0[3], k1[3];
   out.illcond = !plane_whitening<T>(mu, Rc, s, k0, k1);
   T scl = mu[2] / c;  // normalise so that y2 = 1 on the centre ray
-  out.G[0] = float(k0[0] * T(cam.ifx) * scl);
-  out.G[1] = float(k0[1] * T(cam.ify) * scl);
-  out.G[2] = float(k1[0] * T(cam.ifx) * scl);
-  out.G[3] = float(k1[1] * T(cam.ify) * scl);
+  // the record's G carries sqrt(kp), so that the rasteriser's support test kp q <= r reads
+  // q' <= r with q' = |G delta|^2
+  const T gsc = scl * t_sqrt((c2 - kappa) / kappa);
+  out.G[0] = float(k0[0] * T(cam.ifx) * gsc);
+  out.G[1] = float(k0[1] * T(cam.ify) * gsc);
+  out.G[2] = float(k1[0] * T(cam.ifx) * gsc);
+  out.G[3] = float(k1[1] * T(cam.ify) * gsc);
   // y2 = mu^T Sigma^-1 x / c; Sigma^-1 mu = sum_k n_k m_k / s_k.
   T w0 = Rc[0] * m[0] / s[0] + Rc[1] * m[1] / s[1] + Rc[2] * m[2] / s[2];
   T w1 = Rc[3] * m[0] / s[0] + Rc[4] * m[1] / s[1] + Rc[5] * m[2] / s[2];
@@ -238,6 +254,7 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
     const T det = M00 * M11 - M01 * M01;
     out.rho = -1.f;
     out.M00 = -1.f;  // no bounded ellipse unless set below
+    bool bounded = false;
     if (M00 > T(0) && M11 > T(0) && det > T(1e-4) * M00 * M11) {
       const T dc0 = (M11 * hh0 - M01 * hh1) / det, dc1 = (M00 * hh1 - M01 * hh0) / det;
       const T rho = T(1) + hh0 * dc0 + hh1 * dc1;
@@ -245,20 +262,18 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
         out.dc0 = float(dc0); out.dc1 = float(dc1);
         out.M00 = float(M00 / rho); out.M01 = float(M01 / rho); out.M11 = float(M11 / rho);
         out.rho = float(rho); out.det = float(det / (rho * rho));
-        // a bounded support ellipse bounds the pixels even where the quad reaches
-        // behind the camera
+        // the bounding box of a bounded support ellipse bounds the pixels (also where the
+        // quad reaches behind the camera) and is the tightest box of the support: the quad
+        // is not needed then
         const T ucx = T(cam.fx) * mu[0] / mu[2] + T(cam.cx) + dc0;
         const T ucy = T(cam.fy) * mu[1] / mu[2] + T(cam.cy) + dc1;
         const T hx = t_sqrt(rho * T(1.001) * M11 / det), hy = t_sqrt(rho * T(1.001) * M00 / det);
-        if (full) {
-          full = false;
-          xmn = float(ucx - hx); xmx = float(ucx + hx); ymn = float(ucy - hy); ymx = float(ucy + hy);
-        } else {
-          xmn = fmaxf(xmn, float(ucx - hx)); xmx = fminf(xmx, float(ucx + hx));
-          ymn = fmaxf(ymn, float(ucy - hy)); ymx = fminf(ymx, float(ucy + hy));
-        }
+        bounded = true;
+        xmn = float(ucx - hx); xmx = float(ucx + hx); ymn = float(ucy - hy); ymx = float(ucy + hy);
       }
     }
+    // otherwise the support is bounded by the paper's quad (Sec. 4.1)
+    if (!bounded) quad_screen_box<T>(mu, Rc, s, m, c, c2, kappa, cam, full, xmn, xmx, ymn, ymx);
   }
   return tile_rect(full, xmn, xmx, ymn, ymx, cam, tile_w, tile_h, out) ? kKeep : kSkip;
 }
@@ -314,10 +329,12 @@ __device__ int gs_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, co
   const T idet = T(1) / det;
   const T A00 = P11 * idet, A01 = -P01 * idet, A11 = P00 * idet;
   const T g00 = t_sqrt(A00);
-  out.G[0] = float(g00);
-  out.G[1] = float(A01 / g00);
+  // G scaled by sqrt(kp) = 1 / sqrt(kappa), as for RayGS
+  const T isk = T(1) / t_sqrt(kappa);
+  out.G[0] = float(g00 * isk);
+  out.G[1] = float(A01 / g00 * isk);
   out.G[2] = 0.f;
-  out.G[3] = float(T(1) / (t_sqrt(det) * g00));
+  out.G[3] = float(T(1) / (t_sqrt(det) * g00) * isk);
   out.h[0] = 0.f;
   out.h[1] = 0.f;
   out.kp = float(T(1) / kappa);
@@ -598,13 +615,18 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
           const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
           const float z = depth_f32(cam, mx, my, mz);
           if (z > cam.near_z) {
-            df muc[3];
-            mean_cam_df(cam, mx, my, mz, muc);
-            const float mu[3] = {muc[0].hi, muc[1].hi, muc[2].hi};
+            // a float32 camera-frame mean: the cull radius below carries its rounding
+            // (a few ulp of |R m| + |t|) with a wide margin
+            float mu[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+              mu[r] = fmaf(cam.R[3 * r], mx, fmaf(cam.R[3 * r + 1], my, fmaf(cam.R[3 * r + 2], mz, cam.t[r])));
+            const float mag = fabsf(mx) + fabsf(my) + fabsf(mz) + fabsf(cam.t[0]) + fabsf(cam.t[1]) + fabsf(cam.t[2]);
             float s2 = s_s2max[t];
             if (cam.mip)
               s2 += P.mip_sigma2 * (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) / (cam.fx * cam.fy);
-            const float rad = sk * sqrtf(s2) * 1.01f + 1e-5f * (fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2])) + 1e-5f;
+            const float rad = sk * sqrtf(s2) * 1.01f + 1e-5f * (fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2])) +
+                              2e-6f * mag + 1e-5f;
             // the GS support is the linearised projection, not bounded by the sphere's
             // cone: its exact screen box decides in the full stage
             keep = MODE != kStageRay || !outside_frustum<float>(mu, rad, cam);

@@ -33,9 +33,10 @@ struct DevCam {
 
 // 64-byte per-(primitive, view) pixel record consumed by the rasteriser.
 //   a = (u_hi, v_hi, u_lo, v_lo)   projected centre in pixels, double-float
-//   b = (G00, G01, G10, G11)       y01 = G (px - u), scaled so that y2(centre) = 1
+//   b = (G00, G01, G10, G11)       y01' = G (px - u) = sqrt(kp) y01, with y01 scaled so that
+//                                  y2(centre) = 1; q' = |y01'|^2 = kp |y01|^2
 //   c = (h0, h1, kp, c2h)          y2 = 1 + h . (px - u); kp = (c^2-kappa)/kappa;
-//                                  c2h = c^2 log2(e) / 2
+//                                  c2h = c^2 log2(e) / 2; the support is q' <= y2^2, y2 > 0
 //   d = (lo2o, r, g, b)            log2 of the (modulated) opacity; colour
 struct __align__(16) Rec {
   float4 a, b, c, d;

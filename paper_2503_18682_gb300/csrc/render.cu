@@ -11,7 +11,8 @@
 //   D log2(e)/2 = c2h q / (q + r)                     (fragment formula)
 //   omega = min(alpha_max, 2^(log2 o - D log2(e)/2))
 // With the GS divergence of Sec. 3.1 the records carry h = 0 and G with G^T G = Sigma_pi^-1,
-// so that r = 1, the test reads q <= kappa and D log2(e)/2 = c2h q (qmix = 0 below).
+// so that r = 1, the test reads q <= kappa and D log2(e)/2 = c2h q (DIV = 1 below).  The
+// records' G carries sqrt(kp), so that the support test is the single compare q' <= r.
 // A thread's PX pixels lie on one tile row, interleaved with the other threads of that
 // row (columns lx, lx + QX, lx + 2 QX, ...), so that a footprint covering a range of
 // columns hits the same pixel slots k in every lane of the row and the per-slot
@@ -24,7 +25,7 @@
 
 namespace raygs {
 
-template <int TW, int TH, int PX, int NBF, bool COUNT>
+template <int TW, int TH, int PX, int NBF, bool COUNT, int DIV>
 __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P) {
   constexpr int NT = TW * TH / PX;  // threads
   constexpr int NB = NBF * NT;      // records per batch
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
     for (int rr = 0; rr < PER; ++rr) {
       const int slot = tid + rr * NT;
       if (start + slot < rg.y)
-        stage_record(s_raw[slot], ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
+        stage_record<DIV>(s_raw[slot], ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
     }
     __syncthreads();
 #pragma unroll
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(TW *TH / PX, 16) render_kernel(RenderParams P)
       // every pixel, so its image checks the filter
       if (PX >= 8 && !COUNT && !row_may_hit<PX>(A, B, Cc, s_D[j].w, fl_x, fl_y, step)) continue;
       float q[PX], r[PX], y0[PX], y1[PX], y2[PX];
-      uint32_t hit = eval_pixels<PX>(A, B, Cc.x, fl_x, fl_y, step, q, r, y0, y1, y2);
+      uint32_t hit = eval_pixels<PX>(A, B, fl_x, fl_y, step, q, r, y0, y1, y2);
       hit &= alive;
       if (hit) {
         const float4 Dd = s_D[j];
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
           if (hit & (1u << k)) {
-            const float al = fminf(P.alpha_max, pixel_opacity(Cc, q[k], r[k], P.qmix));
+            const float al = fminf(P.alpha_max, pixel_opacity<DIV>(Cc, q[k], r[k]));
             const float w = al * T[k];
             const float Tn = T[k] - w;
             if (Tn < P.t_stop) {
@@ -196,15 +197,20 @@ static unsigned persistent_grid(K kernel, int threads, int num_sms, int n_tiles)
 cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int batch_records, int num_sms,
                           bool count, cudaStream_t st) {
   if (P.n_tiles <= 0) return cudaSuccess;
+  const bool gs = P.qmix == 0.f;  // D_gs records (Sec. 3.1)
+#define RAYGS_RENDER_LAUNCH(TW, TH, PX, NBF, C, D)                                                   \
+  {                                                                                                   \
+    auto k = render_kernel<TW, TH, PX, NBF, C, D>;                                                    \
+    k<<<persistent_grid(k, TW * TH / PX, num_sms, P.n_tiles), TW * TH / PX, 0, st>>>(P);              \
+  }
 #define RAYGS_RENDER_CASE(TW, TH, PX, NBF)                                                             \
   if (tile_w == TW && tile_h == TH && batch_records == NBF) {                                         \
-    constexpr int NT = TW * TH / PX;                                                                  \
-    if (count) {                                                                                      \
-      auto k = render_kernel<TW, TH, PX, NBF, true>;                                                  \
-      k<<<persistent_grid(k, NT, num_sms, P.n_tiles), NT, 0, st>>>(P);                                \
+    if (gs) {                                                                                         \
+      if (count) RAYGS_RENDER_LAUNCH(TW, TH, PX, NBF, true, 1)                                        \
+      else RAYGS_RENDER_LAUNCH(TW, TH, PX, NBF, false, 1)                                             \
     } else {                                                                                          \
-      auto k = render_kernel<TW, TH, PX, NBF, false>;                                                 \
-      k<<<persistent_grid(k, NT, num_sms, P.n_tiles), NT, 0, st>>>(P);                                \
+      if (count) RAYGS_RENDER_LAUNCH(TW, TH, PX, NBF, true, 0)                                        \
+      else RAYGS_RENDER_LAUNCH(TW, TH, PX, NBF, false, 0)                                             \
     }                                                                                                 \
     return cudaGetLastError();                                                                        \
   }
@@ -217,6 +223,7 @@ cudaError_t launch_render(const RenderParams &P, int tile_w, int tile_h, int bat
   RAYGS_RENDER_CASE(32, 16, 8, 2)
   RAYGS_RENDER_CASE(8, 8, 2, 2)
 #undef RAYGS_RENDER_CASE
+#undef RAYGS_RENDER_LAUNCH
   return cudaErrorInvalidValue;
 }
 
