@@ -33,8 +33,6 @@ UNIT = "stereo frames/s (16-view batches/s)"
 WORKLOAD = ("stereo-VR batch: 3M blob primitives (10% axis ratio > 1e3), 16 views "
             "(4 stereo pairs 2064x2208 per eye + 8 random 640-1920 x 480-1080), one CUDA graph")
 
-# algorithmic FP32 flops of the rasteriser (FMA = 2): per evaluated (pixel, primitive) pair
-# and extra per composited pair; see the design notes
 # DRAM bytes (read + write) of one full-size rasteriser launch on the stereo batch, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/render_kernel_*),
 # keyed by tile shape and a digest of the rasteriser's sources: a kernel changed since the
@@ -67,8 +65,11 @@ def render_source_digest(texts=None):
     return h.hexdigest()[:16]
 
 
-FLOP_EVAL = 17
-FLOP_COMP = 15
+# algorithmic FP32 flops of the rasteriser (FMA = 2), the per-unit figures of the scope
+# table's measurement plan: 22 per evaluated (pixel, primitive) pair (the support test's
+# reject path: about 9 FMA and 4 other FP32 operations) and 10 more per composited pair
+FLOP_EVAL = 22
+FLOP_COMP = 10
 
 
 def peaks():
@@ -197,7 +198,34 @@ def cpu_oracle_sample(scene, cams, n_pixels=96, seed=11, threads=0):
     per_batch = len(cams) * t_setup + P * t_pix
     desc = (f"FP64 oracle, {n_pixels} sampled pixels of view 0 against all {scene['means'].shape[0]} "
             f"primitives plus one per-view setup; extrapolated to {len(cams)} views / {P} pixels")
+    cpu_oracle_sample.last_t_pix = t_pix
     return per_batch, cores, desc, t_setup + t_all
+
+
+def cpu_oracle_configs(threads=0):
+    """The FP64 oracle on bounded samples of the other workloads (a baseline, not a target):
+    the 64x64 workload at full frame; the 720p MIP and forward+backward workloads and the
+    precision workload (its 3840x2160 view 0) on sampled pixels, each against all the
+    primitives.  Per workload: (pixel, primitive) pairs per second, counting every pixel
+    against every primitive (a pixel's loop ends at its transmittance stop, so dense views
+    run faster per pair; the per-view setup apart), and the extrapolated seconds per frame,
+    with the cores used."""
+    from paper_2503_18682_gb300 import scenes
+    cores = os.cpu_count() or 1
+    out = {}
+    plans = [("64x64_1k_full_frame", scenes.workload_small, None),
+             ("720p_mip_500k", scenes.workload_mip_720p, 256),
+             ("720p_fwd_bwd_1.5m", scenes.workload_backward_720p, 256),
+             ("precision_6m_4k_view0", scenes.workload_precision, 64)]
+    for name, make, n_pix in plans:
+        scene, cams = make()
+        cam = cams[0]
+        W, H = cam["width"], cam["height"]
+        n = int(scene["means"].shape[0])
+        per_frame, _, desc, _ = cpu_oracle_sample(scene, [cam], n_pixels=n_pix or W * H, threads=threads)
+        out[name] = dict(seconds_per_frame=per_frame, pixel_primitive_pairs_per_s=n / cpu_oracle_sample.last_t_pix,
+                         sample=desc, cores=cores)
+    return out
 
 
 def run_reference(args, world, rank):
@@ -473,10 +501,15 @@ def run_ours(args, world, rank, local):
         context("gs_vs_raygs", lambda: dict(stereo_batch=divergence_ab(st, cams, n, r.cfg, r.capacity, dev),
                                             plain_720p=divergence_ab_720p(r.cfg, dev)))
         context("precision_storage", lambda: precision_storage(args, dev))
+        context("precision_ablation", lambda: precision_ablation(args, dev))
         context("antialiasing", lambda: antialiasing(args, dev))
     if rank == 0 and not args.no_cpu_baseline:
         spb, cores, desc, _ = cpu_oracle_sample(scene, cams, n_pixels=args.ref_pixels)
         line["cpu_baseline"] = dict(value=1.0 / spb, unit=UNIT, cores=cores, kind="oracle", sample=desc)
+        try:
+            line["cpu_baseline"]["other_workloads"] = cpu_oracle_configs()
+        except Exception as ex:  # noqa: BLE001 - reported, not hidden
+            line["cpu_baseline"]["other_workloads"] = dict(error=f"{type(ex).__name__}: {str(ex)[:200]}")
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -653,19 +686,33 @@ def antialiasing(args, dev):
                 mip_exact_vs_supersampled=err(img_mipx), mip_vs_mip_exact=err(img_mip, img_mipx))
 
 
+# storage forms of the precision workload: SH / log-scale / opacity dtypes
+STORAGE_FORMS = {"f32": ("f32", "f32", "f32"), "f16": ("f16", "f16", "f16"), "bf16": ("bf16", "bf16", "f16"),
+                 "sh_f16": ("f16", "f32", "f32")}
+
+
+def _image_err(a, b):
+    import torch
+    d = (a - b).abs()
+    mse = float(((a - b).double() ** 2).mean())
+    return dict(max_abs=float(d.max()), psnr_db=(99.0 if mse == 0 else -10 * np.log10(mse)),
+                frac_pixels_over_1e3=float((d.max(dim=1).values > 1e-3).double().mean()))
+
+
 def precision_storage(args, dev):
     """The 6M-primitive precision workload (4 views at 3840x2160 plus the same poses at
-    960x540 with the MIP filter) with SH and log-scales stored in FP16 or BF16 and opacity
-    logits in FP16, against the FP32 form on the same GPU: forward time of each form and
-    the image error of the reduced forms (max-abs over the RGB channels, PSNR for a unit
-    range).  All arithmetic is FP32 in every form."""
+    960x540 with the MIP filter) in four storage forms: FP32; SH, log-scales and opacity
+    logits in FP16; SH and log-scales in BF16 with FP16 opacity; SH alone in FP16.  Per form:
+    forward time, attribute bytes and the image error against the FP32 form on the same GPU
+    (max-abs over the RGB channels, PSNR for a unit range, share of pixels over 1e-3).  All
+    arithmetic is FP32 in every form."""
     import torch
     from paper_2503_18682_gb300 import raygs, scenes
     scene, cams = scenes.workload_precision()
     n = int(scene["means"].shape[0])
     out, ref = {}, None
-    for form in ("f32", "f16", "bf16"):
-        sc_np = scene if form == "f32" else scenes.to_storage(scene, form)
+    for form, (sh, sc_dt, op) in STORAGE_FORMS.items():
+        sc_np = scene if form == "f32" else scenes.to_storage_form(scene, sh=sh, scales=sc_dt, opacity=op)
         st = raygs.scene_to_device(sc_np, dev)
         attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
         r = raygs.Renderer(cams, n, device=dev)
@@ -688,18 +735,53 @@ def precision_storage(args, dev):
             fwd()
         e1.record()
         e1.synchronize()
-        entry = dict(forward_ms=e0.elapsed_time(e1) / 3, attribute_bytes=int(attr_bytes))
+        entry = dict(dtypes=dict(sh=sh, log_scales=sc_dt, opacity_logits=op), forward_ms=e0.elapsed_time(e1) / 3,
+                     attribute_bytes=int(attr_bytes))
         if ref is None:
             ref = rgb.clone()
         else:
-            d = (rgb - ref).abs()
-            mse = float(((rgb - ref).double() ** 2).mean())
-            entry.update(max_abs_vs_f32=float(d.max()), psnr_vs_f32_db=(99.0 if mse == 0 else -10 * np.log10(mse)),
-                         frac_pixels_over_1e3=float((d.max(dim=1).values > 1e-3).double().mean()))
+            entry["vs_f32"] = _image_err(rgb, ref)
         out[form] = entry
         del r, st, rgb, T, nc
         torch.cuda.empty_cache()
     out["workload"] = f"{n} blob primitives, 4 views 3840x2160 + the same 4 poses at 960x540 with MIP"
+    return out
+
+
+def precision_ablation(args, dev):
+    """Each attribute group rounded alone to FP16 or BF16 (the values its reduced storage
+    would hold, rendered through the FP32 path, which gives the same image as the reduced
+    storage itself: the conversion on load is exact), against the unrounded FP32 image: the
+    precision workload's generator at 200k primitives, its 8 poses at a quarter of the size
+    (960x540 and 240x135 with MIP)."""
+    import torch
+    from paper_2503_18682_gb300 import raygs, scenes
+    scene = scenes.blob_scene(200_000, seed=4)
+    cams = []
+    for c in scenes.precision_cameras(seed=4):
+        w, h = c["width"] // 4, c["height"] // 4
+        cams.append(scenes.make_camera(w, h, float(c["fx"]) / 4, float(c["fy"]) / 4, R=c["R"], t=c["t"],
+                                       mip=c["mip"]))
+    n = int(scene["means"].shape[0])
+    r = raygs.Renderer(cams, n, device=dev)
+
+    def render(sc):
+        rgb, _, _ = r.forward(raygs.scene_to_device(sc, dev))
+        torch.cuda.synchronize()
+        return rgb.clone()
+
+    ref = render(scene)
+    cases = {"sh_dc": dict(sh_dc=None), "sh_rest": dict(sh_rest=None), "log_scales": dict(scales=None),
+             "opacity_logits": dict(opacity=None)}
+    out = {}
+    for name, kw in cases.items():
+        for dt in ("f16", "bf16"):
+            if name == "opacity_logits" and dt == "bf16":
+                continue
+            args_ = {k: dt for k in kw}
+            out[f"{name}_{dt}"] = _image_err(render(scenes.round_attributes(scene, **args_)), ref)
+    out["all_sh_f16"] = _image_err(render(scenes.round_attributes(scene, sh_dc="f16", sh_rest="f16")), ref)
+    out["workload"] = f"{n} blob primitives, the 8 precision poses at 960x540 / 240x135 (MIP)"
     return out
 
 
@@ -822,7 +904,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=3_000_000)
-    ap.add_argument("--ref-pixels", type=int, default=256)
+    ap.add_argument("--ref-pixels", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="keep the raw clock samples of the timed region here")
     ap.add_argument("--no-backward", action="store_true")

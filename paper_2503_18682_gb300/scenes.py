@@ -218,25 +218,62 @@ def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
     return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(F32)
 
 
+def _store(x: np.ndarray, dtype: str):
+    if dtype == "f32":
+        return np.asarray(x, dtype=F32)
+    if dtype == "f16":
+        return np.asarray(x, dtype=F32).astype(np.float16)
+    if dtype == "bf16":
+        return f32_to_bf16_bits(x)
+    raise ValueError(dtype)
+
+
+def to_storage_form(scene: dict, sh: str = "f32", scales: str = "f32", opacity: str = "f32") -> dict:
+    """Store SH coefficients, log-scales and opacity logits each in its own dtype ('f32',
+    'f16' or 'bf16'; opacity 'f32' or 'f16').  Reduced fields are numpy float16 arrays
+    ('f16') or uint16 bf16 bit patterns ('bf16'), tagged ``sh_dtype``/``scale_dtype``/
+    ``opacity_dtype``."""
+    if opacity not in ("f32", "f16"):
+        raise ValueError(opacity)
+    out = dict(scene)
+    out["sh"], out["sh_dtype"] = _store(scene["sh"], sh), sh
+    out["log_scales"], out["scale_dtype"] = _store(scene["log_scales"], scales), scales
+    out["opacity_logits"], out["opacity_dtype"] = _store(scene["opacity_logits"], opacity), opacity
+    return out
+
+
 def to_storage(scene: dict, dtype: str) -> dict:
     """Store log-scales and SH in ``dtype`` ('f16' or 'bf16') and opacity logits in f16.
 
     Returns a new scene whose reduced fields are numpy float16 arrays ('f16') or uint16
     bf16 bit patterns ('bf16'), with ``scale_dtype``/``sh_dtype``/``opacity_dtype`` tags.
     """
-    out = dict(scene)
-    if dtype == "f16":
-        out["log_scales"] = scene["log_scales"].astype(np.float16)
-        out["sh"] = scene["sh"].astype(np.float16)
-    elif dtype == "bf16":
-        out["log_scales"] = f32_to_bf16_bits(scene["log_scales"])
-        out["sh"] = f32_to_bf16_bits(scene["sh"])
-    else:
+    if dtype not in ("f16", "bf16"):
         raise ValueError(dtype)
-    out["opacity_logits"] = scene["opacity_logits"].astype(np.float16)
-    out["scale_dtype"] = dtype
-    out["sh_dtype"] = dtype
-    out["opacity_dtype"] = "f16"
+    return to_storage_form(scene, sh=dtype, scales=dtype, opacity="f16")
+
+
+def round_attributes(scene: dict, sh_dc: str = "f32", sh_rest: str = "f32", scales: str = "f32",
+                     opacity: str = "f32") -> dict:
+    """The float32 scene whose chosen attribute groups are rounded to 'f16' or 'bf16' (SH DC
+    coefficient, higher SH bands, log-scales, opacity logits): the values a reduced storage
+    of just those groups would hold, kept in float32 (an ablation of the storage rounding)."""
+    def rnd(x, dt):
+        x = np.asarray(x, dtype=F32)
+        if dt == "f32":
+            return x.copy()
+        if dt == "f16":
+            return x.astype(np.float16).astype(F32)
+        if dt == "bf16":
+            return bf16_bits_to_f32(f32_to_bf16_bits(x))
+        raise ValueError(dt)
+    out = dict(scene)
+    sh = np.array(scene["sh"], dtype=F32)
+    sh[:, :1] = rnd(sh[:, :1], sh_dc)
+    sh[:, 1:] = rnd(sh[:, 1:], sh_rest)
+    out["sh"] = sh
+    out["log_scales"] = rnd(scene["log_scales"], scales)
+    out["opacity_logits"] = rnd(scene["opacity_logits"], opacity)
     return out
 
 
