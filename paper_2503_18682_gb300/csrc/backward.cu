@@ -54,14 +54,18 @@ __device__ __forceinline__ int warp_sum16_component(int lane) {
 }
 
 template <int TW, int TH, int PX>
-__global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams P) {
+__global__ void __launch_bounds__(TW *TH / PX, (PX >= 8 ? 512 : 896) / (TW * TH / PX)) render_backward_kernel(BackParams P) {
   constexpr int NT = TW * TH / PX;
-  constexpr int NB = 2 * NT;
+  constexpr int NB = NT;
   constexpr int QX = TW / PX;
   constexpr int NW = NT / 32;
   __shared__ float4 s_A[NB], s_B[NB], s_C[NB], s_D[NB];
+  __shared__ float s_isk[NB];  // 1 / sqrt(kp) of each staged record
   __shared__ uint32_t s_e[NB];
   __shared__ float s_acc[NB][kGradW];
+  // per pixel slot (thread-major): final T and the loss gradients, read on every hit
+  __shared__ float4 s_g[PX][NT];
+  __shared__ float s_tfin[PX][NT];
   __shared__ int s_view, s_lmax;
   const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -82,20 +86,19 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
   const float ox_tile = float(px0) + 0.5f, oy_tile = float(py0) + 0.5f;
   const float fl_x = float(lx), fl_y = float(ly), step = float(QX);
 
-  float Tk[PX], Tfin[PX], S0[PX], S1[PX], S2[PX], g0[PX], g1[PX], g2[PX], gT[PX];
+  float Tk[PX], S0[PX], S1[PX], S2[PX];
   int last[PX];
   int lmax = 0;
 #pragma unroll
   for (int k = 0; k < PX; ++k) {
     const bool in = py < cam.H && px + k * QX < cam.W;
     const long long pix = cam.pix_base + (long long)py * cam.W + px + k * QX;
-    Tfin[k] = in ? P.Tf[pix] : 1.f;
-    Tk[k] = Tfin[k];
+    const float tf = in ? P.Tf[pix] : 1.f;
+    s_tfin[k][tid] = tf;
+    Tk[k] = tf;
     last[k] = in ? P.ncontrib[pix] : 0;
-    g0[k] = in ? P.dL_drgb[3 * pix] : 0.f;
-    g1[k] = in ? P.dL_drgb[3 * pix + 1] : 0.f;
-    g2[k] = in ? P.dL_drgb[3 * pix + 2] : 0.f;
-    gT[k] = (in && P.dL_dT) ? P.dL_dT[pix] : 0.f;
+    s_g[k][tid] = make_float4(in ? P.dL_drgb[3 * pix] : 0.f, in ? P.dL_drgb[3 * pix + 1] : 0.f,
+                              in ? P.dL_drgb[3 * pix + 2] : 0.f, (in && P.dL_dT) ? P.dL_dT[pix] : 0.f);
     S0[k] = S1[k] = S2[k] = 0.f;
     lmax = max(lmax, last[k]);
   }
@@ -118,6 +121,7 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       const uint32_t pos = P.inst_vals[rg.x + start + slot];
       const Rec r = P.rec[P.pairs[pos]];
       stage_record<0>(r, ox_tile, oy_tile, s_A[slot], s_B[slot], s_C[slot], s_D[slot]);
+      s_isk[slot] = rsqrtf(r.c.z);
       s_e[slot] = emission_index(P, pos, ty, tx);
     }
     for (int i = tid; i < nb * kGradW; i += NT) (&s_acc[0][0])[i] = 0.f;
@@ -136,24 +140,26 @@ __global__ void __launch_bounds__(TW *TH / PX) render_backward_kernel(BackParams
       for (int c = 0; c < kGradW; ++c) acc[c] = 0.f;
       bool any = false;
       // the staged G carries sqrt(kp): y01 = y01' / sqrt(kp), q = q' / kp
-      const float ikp = hit ? 1.f / Cs.x : 0.f, isk = hit ? sqrtf(ikp) : 0.f;
+      const float isk = s_isk[j], ikp = isk * isk;
 #pragma unroll
       for (int k = 0; k < PX; ++k) {
         if ((hit & (1u << k)) && pos < last[k]) {
           any = true;
+          const float4 gg = s_g[k][tid];
+          const float g0 = gg.x, g1 = gg.y, g2 = gg.z, gT = gg.w, Tfin = s_tfin[k][tid];
           const float4 Cc = s_C[j], Dd = s_D[j];
           const float raw = pixel_opacity<0>(Cc, q[k], r[k]);
           const bool clamped = raw > P.alpha_max;
           const float om = clamped ? P.alpha_max : raw;
           const float onem = 1.f - om;
           const float Ti = Tk[k] / onem;
-          const float gc = g0[k] * Dd.x + g1[k] * Dd.y + g2[k] * Dd.z;
-          const float gS = g0[k] * S0[k] + g1[k] * S1[k] + g2[k] * S2[k];
-          const float dLdw = Ti * gc - (gS + gT[k] * Tfin[k]) / onem;
+          const float gc = g0 * Dd.x + g1 * Dd.y + g2 * Dd.z;
+          const float gS = g0 * S0[k] + g1 * S1[k] + g2 * S2[k];
+          const float dLdw = Ti * gc - (gS + gT * Tfin) / onem;
           const float wT = om * Ti;
-          acc[10] += g0[k] * wT;
-          acc[11] += g1[k] * wT;
-          acc[12] += g2[k] * wT;
+          acc[10] += g0 * wT;
+          acc[11] += g1 * wT;
+          acc[12] += g2 * wT;
           S0[k] = fmaf(Dd.x, wT, S0[k]);
           S1[k] = fmaf(Dd.y, wT, S1[k]);
           S2[k] = fmaf(Dd.z, wT, S2[k]);
@@ -303,10 +309,17 @@ __device__ void view_whitening(const float muf[3], const df muc[3], const T Rp[9
   for (int i = 0; i < 9; ++i) Rc_out[i] = float(Rc[i]);
 }
 
+constexpr int kParamThreads = 64;
+
 // Chain rule of one primitive over the views where it is visible; SH gradients are
-// accumulated into dsh, the other parameter gradients written directly.
-template <int DEG>
-__device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g, const float *coef, float *dsh) {
+// accumulated into dsh (this thread's row of shared memory), the other parameter
+// gradients written directly.
+// FP64 = false handles the primitives that need no FP64 whitening in any view and returns
+// false for the others without writing anything; FP64 = true handles exactly those (the
+// near-degenerate ones), so that the FP64 code holds no registers in the common kernel.
+template <int DEG, bool FP64>
+__device__ __forceinline__ bool param_grads_one(const ParamGradParams &P, int g, const float *coef, float *dsh,
+                                                int dsh_stride = 1) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   const float mx = P.means[3 * int64_t(g)], my = P.means[3 * int64_t(g) + 1], mz = P.means[3 * int64_t(g) + 2];
   float ls[3], q4[4];
@@ -322,11 +335,7 @@ __device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g,
     const float lmax = fmaxf(fmaxf(ls[0], ls[1]), ls[2]), lmin = fminf(fminf(ls[0], ls[1]), ls[2]);
     degenerate = (lmax - lmin) > logf(P.degenerate_ratio);
   }
-  double Rpd[9], sd[3];
-  if (degenerate) {
-    quat_rot<double>(double(q4[0]), double(q4[1]), double(q4[2]), double(q4[3]), Rpd);
-    for (int k = 0; k < 3; ++k) sd[k] = exp(double(ls[k]));
-  }
+  if (degenerate != FP64) return false;
 
   float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dRp[9], dlogit = 0.f;
 #pragma unroll
@@ -355,8 +364,14 @@ __device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g,
       const bool ok = plane_whitening<float>(muf, Rcf, s, k0, k1);
       use_fp64 = P.fp64_degenerate == 2 || !ok;
     }
-    if (use_fp64) view_whitening<double>(muf, muc, Rpd, sd, cam, Km, Sig, Rc);
-    else view_whitening<float>(muf, muc, Rp, s, cam, Km, Sig, Rc);
+    if (FP64 && use_fp64) {
+      double Rpd[9], sd[3];
+      quat_rot<double>(double(q4[0]), double(q4[1]), double(q4[2]), double(q4[3]), Rpd);
+      for (int k = 0; k < 3; ++k) sd[k] = exp(double(ls[k]));
+      view_whitening<double>(muf, muc, Rpd, sd, cam, Km, Sig, Rc);
+    } else {
+      view_whitening<float>(muf, muc, Rp, s, cam, Km, Sig, Rc);
+    }
     // dL/dmu_c = -2 K^T a
     float dmuc[3];
 #pragma unroll
@@ -410,23 +425,28 @@ __device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g,
     const float ex = mx - cam.C[0], ey = my - cam.C[1], ez = mz - cam.C[2];
     const float inv_len = rsqrtf(ex * ex + ey * ey + ez * ez);
     const float dx = ex * inv_len, dy = ey * inv_len, dz = ez * inv_len;
-    float Y[16], dY[16][3];
-    sh_basis_grad<DEG>(dx, dy, dz, Y, dY);
+    // the colour before its clamp at 0 (each basis term recomputed where it is used, so that
+    // no per-term arrays stay live), then the gradients of the channels above the clamp
+    float val[3] = {coef[0], coef[1], coef[2]};
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      float Yk, ax, ay, az;
+      sh_term(k, dx, dy, dz, Yk, ax, ay, az);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) val[ch] = fmaf(Yk, coef[3 * k + ch], val[ch]);
+    }
+    const float cl[3] = {val[0] > 0.f ? col[0] : 0.f, val[1] > 0.f ? col[1] : 0.f, val[2] > 0.f ? col[2] : 0.f};
     float gd[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float val = 0.f;
+    for (int k = 0; k < K; ++k) {
+      float Yk, ax, ay, az;
+      sh_term(k, dx, dy, dz, Yk, ax, ay, az);
 #pragma unroll
-      for (int k = 0; k < K; ++k) val += Y[k] * coef[3 * k + ch];
-      if (val > 0.f) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          dsh[3 * k + ch] += col[ch] * Y[k];
-          gd[0] += col[ch] * coef[3 * k + ch] * dY[k][0];
-          gd[1] += col[ch] * coef[3 * k + ch] * dY[k][1];
-          gd[2] += col[ch] * coef[3 * k + ch] * dY[k][2];
-        }
-      }
+      for (int ch = 0; ch < 3; ++ch) dsh[(3 * k + ch) * dsh_stride] += cl[ch] * Yk;
+      const float sk = cl[0] * coef[3 * k] + cl[1] * coef[3 * k + 1] + cl[2] * coef[3 * k + 2];
+      gd[0] = fmaf(sk, ax, gd[0]);
+      gd[1] = fmaf(sk, ay, gd[1]);
+      gd[2] = fmaf(sk, az, gd[2]);
     }
     const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
     dmu[0] += (gd[0] - dx * dd) * inv_len;
@@ -460,43 +480,76 @@ __device__ __forceinline__ void param_grads_one(const ParamGradParams &P, int g,
     P.d_quats[4 * int64_t(g) + 3] = (gz - z * dot) * qn;
   }
   if (P.d_logits) P.d_logits[g] = dlogit;
+  return true;
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(128) param_grads_kernel(ParamGradParams P) {
+__global__ void __launch_bounds__(kParamThreads, 8) param_grads_kernel(ParamGradParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int K3 = 3 * K, SHP = K3 + 1;  // padded row
   // SH coefficients in and their gradients out go through shared memory with coalesced
-  // 16-byte transfers (one row of 3K values per primitive)
-  __shared__ float s_sh[128 * SHP];
+  // 16-byte transfers (one row of 3K values per primitive); the gradients accumulate over
+  // the views in shared memory too
+  __shared__ float s_sh[kParamThreads * SHP];
+  __shared__ float s_dsh[kParamThreads * SHP];
+  __shared__ uint8_t s_keep[kParamThreads];
   const int g0 = blockIdx.x * blockDim.x;
   const int nb = min(int(blockDim.x), P.n - g0);
   stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, 1);
+  float *dsh = s_dsh + threadIdx.x * SHP;
+  for (int i = 0; i < K3; ++i) dsh[i] = 0.f;
   __syncthreads();
   const int g = g0 + threadIdx.x;
   const bool active = g < P.n;
   const float *coef = s_sh + threadIdx.x * SHP;
-  float dsh[3 * K];
-  for (int i = 0; i < 3 * K; ++i) dsh[i] = 0.f;
-  if (active) param_grads_one<DEG>(P, g, coef, dsh);
+  // a primitive left to the FP64 kernel keeps its SH gradients out of the coalesced store
+  s_keep[threadIdx.x] = active && param_grads_one<DEG, false>(P, g, coef, dsh) ? 1 : 0;
   __syncthreads();
   if (P.d_sh) {
-    if (active)
-      for (int k = 0; k < K3; ++k) s_sh[threadIdx.x * SHP + k] = dsh[k];
-    __syncthreads();
     float *dst = P.d_sh + int64_t(g0) * K3;
-    for (int e = threadIdx.x; e < nb * K3; e += blockDim.x) dst[e] = s_sh[(e / K3) * SHP + e % K3];
+    for (int e = threadIdx.x; e < nb * K3; e += blockDim.x)
+      if (s_keep[e / K3]) dst[e] = s_dsh[(e / K3) * SHP + e % K3];
+  }
+}
+
+// The near-degenerate primitives (FP64 whitening in the views where the float32 one is
+// ill-conditioned), grid-stride with direct loads: few enough that coalescing does not
+// matter.  SH gradients accumulate in place in the output (zeroed first).
+template <int DEG>
+__global__ void __launch_bounds__(128) param_grads_fp64_kernel(ParamGradParams P) {
+  constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
+  const float lim = logf(P.degenerate_ratio);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.n; g += gridDim.x * blockDim.x) {
+    float l[3];
+    for (int k = 0; k < 3; ++k) l[k] = load_attr(P.log_scales, 3 * int64_t(g) + k, P.scale_dtype);
+    if (!(fmaxf(fmaxf(l[0], l[1]), l[2]) - fminf(fminf(l[0], l[1]), l[2]) > lim)) continue;
+    float coef[K3];
+    for (int k = 0; k < K3; ++k) coef[k] = load_attr(P.sh, int64_t(g) * K3 + k, P.sh_dtype);
+    float dsh[K3];
+    for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
+    if (param_grads_one<DEG, true>(P, g, coef, dsh) && P.d_sh)
+      for (int k = 0; k < K3; ++k) P.d_sh[int64_t(g) * K3 + k] = dsh[k];
   }
 }
 
 cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st) {
   if (P.n == 0) return cudaSuccess;
-  const int blocks = (P.n + 127) / 128;
+  const int blocks = (P.n + kParamThreads - 1) / kParamThreads;
   switch (P.sh_degree) {
-    case 0: param_grads_kernel<0><<<blocks, 128, 0, st>>>(P); break;
-    case 1: param_grads_kernel<1><<<blocks, 128, 0, st>>>(P); break;
-    case 2: param_grads_kernel<2><<<blocks, 128, 0, st>>>(P); break;
-    default: param_grads_kernel<3><<<blocks, 128, 0, st>>>(P); break;
+    case 0: param_grads_kernel<0><<<blocks, kParamThreads, 0, st>>>(P); break;
+    case 1: param_grads_kernel<1><<<blocks, kParamThreads, 0, st>>>(P); break;
+    case 2: param_grads_kernel<2><<<blocks, kParamThreads, 0, st>>>(P); break;
+    default: param_grads_kernel<3><<<blocks, kParamThreads, 0, st>>>(P); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !P.fp64_degenerate) return e;
+  const int64_t want = (int64_t(P.n) + 127) / 128, cap = int64_t(P.num_sms > 0 ? P.num_sms : 1) * 8;
+  const int gb = int(want < cap ? want : cap);
+  switch (P.sh_degree) {
+    case 0: param_grads_fp64_kernel<0><<<gb, 128, 0, st>>>(P); break;
+    case 1: param_grads_fp64_kernel<1><<<gb, 128, 0, st>>>(P); break;
+    case 2: param_grads_fp64_kernel<2><<<gb, 128, 0, st>>>(P); break;
+    default: param_grads_fp64_kernel<3><<<gb, 128, 0, st>>>(P); break;
   }
   return cudaGetLastError();
 }

@@ -392,6 +392,7 @@ cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T
   R.d_quats = grads.d_quats;
   R.d_logits = grads.d_opacity_logits;
   R.d_sh = grads.d_sh;
+  R.num_sms = w.num_sms;
   return launch_param_grads(R, st);
 }
 

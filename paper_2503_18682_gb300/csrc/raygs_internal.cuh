@@ -318,6 +318,7 @@ struct ParamGradParams {
   const uint32_t *depth_key;
   const float *pg;
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+  int num_sms;
 };
 
 // Records e as the thread's last CUDA error (read back by raygs_last_cuda_error).

@@ -157,6 +157,38 @@ __device__ __forceinline__ void sh_colour(const float *coef, float x, float y, f
   for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
 }
 
+// One real SH basis term k (0 .. 15; term 0 is the colour's constant 1) and its gradient
+// with respect to the direction components (x, y, z), the same functions as sh_colour.
+// Called with a compile-time k inside unrolled loops, so that the switch folds away.
+__device__ __forceinline__ void sh_term(int k, float x, float y, float z, float &Y, float &gx, float &gy, float &gz) {
+  const float c1 = 0.4886025119029199f;
+  const float c2a = 1.0925484305920792f, c2b = 0.31539156525252005f, c2c = 0.5462742152960396f;
+  const float c3a = 0.5900435899266435f, c3b = 2.890611442640554f, c3c = 0.4570457994644658f;
+  const float c3d = 0.3731763325901154f, c3e = 1.445305721320277f;
+  gx = gy = gz = 0.f;
+  switch (k) {
+    case 0: Y = 1.f; break;
+    case 1: Y = c1 * y; gy = c1; break;
+    case 2: Y = c1 * z; gz = c1; break;
+    case 3: Y = c1 * x; gx = c1; break;
+    case 4: Y = c2a * x * y; gx = c2a * y; gy = c2a * x; break;
+    case 5: Y = c2a * y * z; gy = c2a * z; gz = c2a * y; break;
+    case 6: Y = c2b * (3.f * z * z - 1.f); gz = 6.f * c2b * z; break;
+    case 7: Y = c2a * x * z; gx = c2a * z; gz = c2a * x; break;
+    case 8: Y = c2c * (x * x - y * y); gx = 2.f * c2c * x; gy = -2.f * c2c * y; break;
+    case 9: Y = c3a * y * (3.f * x * x - y * y); gx = 6.f * c3a * x * y; gy = 3.f * c3a * (x * x - y * y); break;
+    case 10: Y = c3b * x * y * z; gx = c3b * y * z; gy = c3b * x * z; gz = c3b * x * y; break;
+    case 11: Y = c3c * y * (5.f * z * z - 1.f); gy = c3c * (5.f * z * z - 1.f); gz = 10.f * c3c * y * z; break;
+    case 12: Y = c3d * z * (5.f * z * z - 3.f); gz = c3d * (15.f * z * z - 3.f); break;
+    case 13: Y = c3c * x * (5.f * z * z - 1.f); gx = c3c * (5.f * z * z - 1.f); gz = 10.f * c3c * x * z; break;
+    case 14:
+      Y = c3e * z * (x * x - y * y);
+      gx = 2.f * c3e * x * z; gy = -2.f * c3e * y * z; gz = c3e * (x * x - y * y);
+      break;
+    default: Y = c3a * x * (x * x - 3.f * y * y); gx = 3.f * c3a * (x * x - y * y); gy = -6.f * c3a * x * y; break;
+  }
+}
+
 // Real SH basis values Y[k] (k = 1 .. (DEG+1)^2 - 1; Y[0] is the colour's constant 1) and
 // their gradients dY[k] with respect to the (unnormalised) direction components.
 template <int DEG>
