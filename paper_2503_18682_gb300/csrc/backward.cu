@@ -503,7 +503,9 @@ __global__ void __launch_bounds__(kParamThreads, 8) param_grads_kernel(ParamGrad
   const bool active = g < P.n;
   const float *coef = s_sh + threadIdx.x * SHP;
   // a primitive left to the FP64 kernel keeps its SH gradients out of the coalesced store
-  s_keep[threadIdx.x] = active && param_grads_one<DEG, false>(P, g, coef, dsh) ? 1 : 0;
+  const bool done = active && param_grads_one<DEG, false>(P, g, coef, dsh);
+  s_keep[threadIdx.x] = done ? 1 : 0;
+  if (active && !done) P.fp64_list[atomicAdd(P.fp64_count, 1u)] = uint32_t(g);
   __syncthreads();
   if (P.d_sh) {
     float *dst = P.d_sh + int64_t(g0) * K3;
@@ -513,16 +515,14 @@ __global__ void __launch_bounds__(kParamThreads, 8) param_grads_kernel(ParamGrad
 }
 
 // The near-degenerate primitives (FP64 whitening in the views where the float32 one is
-// ill-conditioned), grid-stride with direct loads: few enough that coalescing does not
-// matter.  SH gradients accumulate in place in the output (zeroed first).
+// ill-conditioned) that param_grads_kernel listed, grid-stride with direct loads: few
+// enough that coalescing does not matter.
 template <int DEG>
 __global__ void __launch_bounds__(128) param_grads_fp64_kernel(ParamGradParams P) {
   constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
-  const float lim = logf(P.degenerate_ratio);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.n; g += gridDim.x * blockDim.x) {
-    float l[3];
-    for (int k = 0; k < 3; ++k) l[k] = load_attr(P.log_scales, 3 * int64_t(g) + k, P.scale_dtype);
-    if (!(fmaxf(fmaxf(l[0], l[1]), l[2]) - fminf(fminf(l[0], l[1]), l[2]) > lim)) continue;
+  const uint32_t count = *P.fp64_count;
+  for (uint32_t li = blockIdx.x * blockDim.x + threadIdx.x; li < count; li += gridDim.x * blockDim.x) {
+    const int g = int(P.fp64_list[li]);
     float coef[K3];
     for (int k = 0; k < K3; ++k) coef[k] = load_attr(P.sh, int64_t(g) * K3 + k, P.sh_dtype);
     float dsh[K3];
@@ -543,7 +543,7 @@ cudaError_t launch_param_grads(const ParamGradParams &P, cudaStream_t st) {
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !P.fp64_degenerate) return e;
-  const int64_t want = (int64_t(P.n) + 127) / 128, cap = int64_t(P.num_sms > 0 ? P.num_sms : 1) * 8;
+  const int64_t want = (int64_t(P.n) + 127) / 128, cap = int64_t(P.num_sms > 0 ? P.num_sms : 1) * 2;
   const int gb = int(want < cap ? want : cap);
   switch (P.sh_degree) {
     case 0: param_grads_fp64_kernel<0><<<gb, 128, 0, st>>>(P); break;

@@ -393,6 +393,9 @@ cudaError_t run_backward(const Work &w, const raygs_scene &scene, const float *T
   R.d_logits = grads.d_opacity_logits;
   R.d_sh = grads.d_sh;
   R.num_sms = w.num_sms;
+  R.fp64_list = w.at<uint32_t>(w.L.deg);
+  R.fp64_count = w.at<uint32_t>(w.L.degc);
+  if ((e = cudaMemsetAsync(R.fp64_count, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
   return launch_param_grads(R, st);
 }
 

@@ -319,6 +319,8 @@ struct ParamGradParams {
   const float *pg;
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
   int num_sms;
+  uint32_t *fp64_list;   // primitives left to the FP64 kernel (the forward's FP64 pair list,
+  uint32_t *fp64_count;  // free by the time of the backward) and their count (zeroed first)
 };
 
 // Records e as the thread's last CUDA error (read back by raygs_last_cuda_error).
