@@ -433,7 +433,7 @@ def run_ours(args, world, rank, local):
     peak_tf = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     ach_tf = flops / (stages["render_ms"] * 1e-3) / 1e12
     # HBM view of the vertex stage: attributes read once; per visible pair the 64-B record,
-    # 8-B tile rectangle and 32-B support ellipse written; the 4-B key of every pair
+    # 8-B tile rectangle and 32-B support sector written; the 4-B key of every pair
     attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
     prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
     bin_bytes = binning_bytes(ctr, n * len(cams))

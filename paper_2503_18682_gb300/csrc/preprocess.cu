@@ -4,7 +4,9 @@
 //
 // Outputs per (view v, primitive g), index v*N + g:
 //   depth_key  float32 bits of the view-space centre depth, or kCulled
-//   rect       inclusive screen-tile rectangle covered by the projected quad (Eq. V_ray)
+//   rect       inclusive screen-tile rectangle that bounds the support (the support
+//              ellipse's box, or the projected quad's, Eq. V_ray)
+//   ell        32-byte support sector: the rectangle again and the support ellipse
 //   rec        64-byte pixel record (see Rec): the factors of the fragment formula of
 //              Sec. 4.2 / App. A.4 in a form that is evaluated from the pixel ray
 //
@@ -142,7 +144,7 @@ __device__ __forceinline__ void quad_screen_box(const T mu[3], const T Rc[9], co
 template <typename T>
 __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, const DevCam &cam,
                           float p_min, float mip_sigma2, int tile_w, int tile_h, StageOut &out,
-                          bool apply_mip = true, bool decide = true) {
+                          bool apply_mip = true, bool decide = true, const float *pre = nullptr) {
   const bool band = decide && sizeof(T) == 4;
   const T mu1 = fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]);
   T e_o = T(2e-6);  // relative rounding bound of o (the float32 sigmoid; grows with Eq. mip)
@@ -180,8 +182,11 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
     o *= t_sqrt(ratio * c2 / c2h);
     e_o += T(0.5) * (e2 / c2 + e2h / c2h) + T(1e-6);
   }
-  // Eq. support: kappa = -2 log(p_min / o); skip when kappa <= 0.
-  T kappa = T(2) * t_log(o / T(p_min));
+  // Eq. support: kappa = -2 log(p_min / o); skip when kappa <= 0.  Without the MIP term o
+  // is the primitive's own, and pre = (kappa, log2 o) holds them, computed once per
+  // primitive with the same operations.
+  const bool use_pre = pre && !(apply_mip && cam.mip == RAYGS_MIP_APPROX);
+  T kappa = use_pre ? T(pre[0]) : T(2) * t_log(o / T(p_min));
   if (band && fabs(kappa) <= T(2) * e_o + T(1e-6)) return kUndecided;
   if (!(kappa > T(0))) return kSkip;
 
@@ -193,16 +198,19 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
   }
 
   // Sec. 3.2 Eq. c: c^2 = mu^T Sigma^-1 mu = |S^-1 R^T mu|^2; skip when c^2 <= kappa.
-  T m[3];
+  T m[3], is[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) m[k] = pk[k] / s[k];
+  for (int k = 0; k < 3; ++k) {
+    is[k] = T(1) / s[k];
+    m[k] = pk[k] * is[k];
+  }
   T c2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
   if (band) {
     // each m_k carries the projection's rounding over s_k (large for thin primitives seen
     // from near their plane), kappa that of log o
     T e_c2 = T(1e-6) * (c2 + kappa) + T(2) * e_o;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) e_c2 += T(2) * fabs(m[k]) * (T(kProjErr32) * mu1 / s[k] + T(1e-6) * fabs(m[k]));
+    for (int k = 0; k < 3; ++k) e_c2 += T(2) * fabs(m[k]) * (T(kProjErr32) * mu1 * is[k] + T(1e-6) * fabs(m[k]));
     if (fabs(c2 - kappa) <= e_c2) return kUndecided;
   }
   if (!(c2 > kappa)) return kSkip;
@@ -228,14 +236,14 @@ __device__ int view_stage(const T mu[3], const T Rp[9], const T s_in[3], T o, co
   out.G[2] = float(k1[0] * T(cam.ifx) * gsc);
   out.G[3] = float(k1[1] * T(cam.ify) * gsc);
   // y2 = mu^T Sigma^-1 x / c; Sigma^-1 mu = sum_k n_k m_k / s_k.
-  T w0 = Rc[0] * m[0] / s[0] + Rc[1] * m[1] / s[1] + Rc[2] * m[2] / s[2];
-  T w1 = Rc[3] * m[0] / s[0] + Rc[4] * m[1] / s[1] + Rc[5] * m[2] / s[2];
+  T w0 = Rc[0] * m[0] * is[0] + Rc[1] * m[1] * is[1] + Rc[2] * m[2] * is[2];
+  T w1 = Rc[3] * m[0] * is[0] + Rc[4] * m[1] * is[1] + Rc[5] * m[2] * is[2];
   T sh = mu[2] / c2;
   out.h[0] = float(w0 * T(cam.ifx) * sh);
   out.h[1] = float(w1 * T(cam.ify) * sh);
   out.kp = float((c2 - kappa) / kappa);
   out.c2h = float(c2 * T(0.5 * 1.4426950408889634));
-  out.lo2o = float(t_log(o) * T(1.4426950408889634));
+  out.lo2o = use_pre ? pre[1] : float(t_log(o) * T(1.4426950408889634));
 
   // ---- Screen-space support: with delta = px - u (pixels), D <= kappa and y2 > 0 hold
   // exactly when f(delta) = kp |G delta|^2 - (1 + h.delta)^2 <= 0, a conic
@@ -455,7 +463,7 @@ __device__ int mipx_view_stage(const T mu[3], const T Rp[9], const T s[3], T o, 
 
 __device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t idx, const DevCam &cam,
                                                   const df muc[3], const StageOut &so, const MipxOut &X,
-                                                  const float rgb[3], float z) {
+                                                  const float rgb[3], float z, bool write_key) {
   df Xc = df_div(muc[0], muc[2]);
   df Yc = df_div(muc[1], muc[2]);
   df u = df_add(df_mul_f(Xc, cam.fx), df{cam.cx, 0.f});
@@ -471,8 +479,6 @@ __device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t i
   q.d = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
   P.rec[idx] = r;
   P.recx[idx] = q;
-  P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
-                           uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
   Ell e;
   e.r0 = uint32_t(so.tx0) | (uint32_t(so.ty0) << 16);
   e.r1 = uint32_t(so.tx1) | (uint32_t(so.ty1) << 16);
@@ -480,12 +486,15 @@ __device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t i
   e.cy = v.hi + so.dc1;
   e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
   P.ell[idx] = e;
-  P.depth_key[idx] = __float_as_uint(z);
+  // the rectangle also in its own compact array: the last depth-sort pass and the backward
+  // gather it by pair, and at 8 bytes per pair it largely stays in L2
+  P.rect[idx] = make_uint2(e.r0, e.r1);
+  if (write_key) P.depth_key[idx] = __float_as_uint(z);
 }
 
 __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, const DevCam &cam,
                                              const df muc[3], const StageOut &so, const float rgb[3],
-                                             float z) {
+                                             float z, bool write_key) {
   df X = df_div(muc[0], muc[2]);
   df Yv = df_div(muc[1], muc[2]);
   df u = df_add(df_mul_f(X, cam.fx), df{cam.cx, 0.f});
@@ -496,8 +505,6 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   r.c = make_float4(so.h[0], so.h[1], so.kp, so.c2h);
   r.d = make_float4(so.lo2o, rgb[0], rgb[1], rgb[2]);
   P.rec[idx] = r;
-  P.rect[idx] = make_uint2(uint32_t(so.tx0) | (uint32_t(so.ty0) << 16),
-                           uint32_t(so.tx1) | (uint32_t(so.ty1) << 16));
   Ell e;
   e.r0 = uint32_t(so.tx0) | (uint32_t(so.ty0) << 16);
   e.r1 = uint32_t(so.tx1) | (uint32_t(so.ty1) << 16);
@@ -505,7 +512,10 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   e.cy = v.hi + so.dc1;
   e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
   P.ell[idx] = e;
-  P.depth_key[idx] = __float_as_uint(z);
+  // the rectangle also in its own compact array: the last depth-sort pass and the backward
+  // gather it by pair, and at 8 bytes per pair it largely stays in L2
+  P.rect[idx] = make_uint2(e.r0, e.r1);
+  if (write_key) P.depth_key[idx] = __float_as_uint(z);
 }
 
 // Two passes per chunk of kViewChunk views, so that the expensive stage runs on dense
@@ -522,11 +532,12 @@ enum StageMode { kStageRay = 0, kStageGS = 1, kStageExact = 2 };
 
 template <int MODE, typename T>
 __device__ __forceinline__ int stage_for(const T mu[3], const T Rp[9], const T s[3], T o, const DevCam &cam,
-                                          const PrepParams &P, StageOut &so, MipxOut &mx) {
+                                          const PrepParams &P, StageOut &so, MipxOut &mx,
+                                          const float *pre = nullptr) {
   if (MODE == kStageGS) return gs_view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.tile_w, P.tile_h, so);
   if (MODE == kStageExact)
     return mipx_view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so, mx);
-  return view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so);
+  return view_stage<T>(mu, Rp, s, o, cam, P.p_min, P.mip_sigma2, P.tile_w, P.tile_h, so, true, true, pre);
 }
 
 template <int DEG, int MODE>
@@ -546,6 +557,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   __shared__ float s_R[kPrepThreads * 9];   // rotation of each primitive
   __shared__ float s_s[kPrepThreads * 3];   // scales
   __shared__ float s_o[kPrepThreads];       // prior opacity
+  __shared__ float2 s_pre[kPrepThreads];    // kappa and log2 of the prior opacity
   __shared__ float s_rad[kPrepThreads];     // sqrt(kappa) s_max (0: cull in every view)
   __shared__ float s_s2max[kPrepThreads];   // s_max^2
   __shared__ uint8_t s_deg[kPrepThreads];
@@ -592,6 +604,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       s_o[t] = o;
       // kappa of the unmodulated opacity bounds every view's (the MIP factor is <= 1)
       const float kappa0 = 2.f * logf(o / P.p_min);
+      s_pre[t] = make_float2(kappa0, logf(o) * 1.4426950408889634f);
       const float smax = fmaxf(fmaxf(s0, s1), s2);
       s_s2max[t] = smax * smax;
       // < 0: culled everywhere; an opacity within rounding of p_min goes on to the full
@@ -610,10 +623,11 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       if (t < nb) {
         const float sk = s_rad[t];
         const int64_t idx = int64_t(v) * P.n + g;
+        float z = 0.f;
         if (sk > 0.f) {
           const DevCam &cam = s_cams[v];
           const float mx = s_means[3 * t], my = s_means[3 * t + 1], mz = s_means[3 * t + 2];
-          const float z = depth_f32(cam, mx, my, mz);
+          z = depth_f32(cam, mx, my, mz);
           if (z > cam.near_z) {
             // a float32 camera-frame mean: the cull radius below carries its rounding
             // (a few ulp of |R m| + |t|) with a wide margin
@@ -632,7 +646,10 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
             keep = MODE != kStageRay || !outside_frustum<float>(mu, rad, cam);
           }
         }
-        if (!keep) P.depth_key[idx] = kCulled;
+        // every key of the warp's 32 consecutive pairs at once (full sectors): the depth of
+        // a kept pair (the full stage writes kCulled over it if it culls the pair), the
+        // marker of a culled one
+        P.depth_key[idx] = keep ? __float_as_uint(z) : kCulled;
       }
       const uint32_t ball = __ballot_sync(0xffffffffu, keep);
       int base = 0;
@@ -660,7 +677,8 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       for (int k = 0; k < 9; ++k) Rp[k] = s_R[9 * tt + k];
       StageOut so;
       MipxOut mxo;
-      const int res = stage_for<MODE, float>(mu, Rp, sv, s_o[tt], cam, P, so, mxo);
+      const float pre[2] = {s_pre[tt].x, s_pre[tt].y};
+      const int res = stage_for<MODE, float>(mu, Rp, sv, s_o[tt], cam, P, so, mxo, pre);
       if (res != kKeep) {
         P.depth_key[idx] = kCulled;
         if (res == kUndecided) P.deg_list[atomicAdd(P.deg_count, 1u)] = uint32_t(idx);
@@ -670,8 +688,9 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
       float rgb[3];
       sh_colour<DEG>(s_sh + tt * SHP, dx * dn, dy * dn, dz * dn, rgb);
-      if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z);
-      else write_record(P, idx, cam, muc, so, rgb, z);
+      // (the cull pass wrote this pair's key)
+      if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z, false);
+      else write_record(P, idx, cam, muc, so, rgb, z, false);
       if (s_deg[tt] && (P.fp64_degenerate == 2 || so.illcond)) {
         const uint32_t slot = atomicAdd(P.deg_count, 1u);
         P.deg_list[slot] = uint32_t(idx);
@@ -719,8 +738,8 @@ __global__ void __launch_bounds__(128) preprocess_fp64_kernel(PrepParams P) {
     float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
     float rgb[3];
     sh_colour<DEG>(coef, dx * dn, dy * dn, dz * dn, rgb);
-    if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z);
-    else write_record(P, idx, cam, muc, so, rgb, z);
+    if (MODE == kStageExact) write_record_mipx(P, idx, cam, muc, so, mxo, rgb, z, true);
+    else write_record(P, idx, cam, muc, so, rgb, z, true);
   }
 }
 
