@@ -425,7 +425,7 @@ def run_ours(args, world, rank, local):
     e2e_single_ms = max_over_ranks(timed(e2e_step, max(2, min(args.steps, 10))), world)
     e2e_ms = e2e_single_ms
     if len(plans) >= 2:
-        e2e_ms = max_over_ranks(e2e_pipelined(plans[:2], plan_outputs[0], st, rgb, host, args.steps, dev), world)
+        e2e_ms = max_over_ranks(e2e_pipelined(plans, plan_outputs, st, rgb, host, args.steps, dev), world)
 
     # roofline of the dominant kernel (the rasteriser: plain FP32 ALU work)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -479,7 +479,7 @@ def run_ours(args, world, rank, local):
                              "stream, mean of 5 after warm-up; pairs counted by the instrumented variant"),
         clocks=clocks,
         e2e=dict(value=1e3 / e2e_ms, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
-                 ms_per_step=e2e_ms, batches_in_flight=min(2, len(plans)),
+                 ms_per_step=e2e_ms, batches_in_flight=len(plans),
                  one_batch_at_a_time=dict(value=1e3 / e2e_single_ms, ms_per_step=e2e_single_ms)),
         gpu_launches=int(gpu_launches),
     )
@@ -515,59 +515,70 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def e2e_pipelined(plans, out2, st, rgb, host, steps, dev):
-    """End to end with two batches in flight: each plan gets its own device copy of the
-    inputs and its own image; step i uploads the pinned host inputs into plan i % 2's copy
-    (upload stream), replays that plan's graph (its own stream) and reads its image back
-    into pinned host memory (download stream).  Step i+1's upload and step i-1's download
-    overlap step i's render on the copy engines; every step still carries its own copies.
-    Returns ms per step (events bracketing all streams' work)."""
+def e2e_pipelined(plans, outs, st, rgb, host, steps, dev):
+    """End to end with the plans' batches in flight: each plan (slot) gets its own device
+    copy of the inputs and its own image; step i uploads the pinned host inputs into slot
+    i % S's copy (upload stream), replays that slot's graph (its own stream) and reads its
+    image back into pinned host memory (download stream).  A slot's next upload waits only
+    until its previous graph has run (the inputs are read by the vertex stage, so they are
+    free then), and its next graph waits for its upload and for the read-back of its
+    previous image.  Uploads and read-backs of other steps overlap the renders on the copy
+    engines; every step still carries its own copies.  Returns ms per step (events
+    bracketing all streams' work).  outs: the image buffers of plans[1:]."""
     import torch
     from paper_2503_18682_gb300 import raygs
-    (r0, s0), (r1, s1) = plans
-    st2 = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in st.items()}
-    with torch.cuda.stream(s1):
-        raygs.raygs_graph_capture(r1.plan, raygs.make_scene(st2), *out2, s1)  # now reads copy 2
-    s1.synchronize()
-    slots = [dict(r=r0, gs=s0, st=st, rgb=rgb), dict(r=r1, gs=s1, st=st2, rgb=out2[0])]
-    for sl in slots:
+    slots = []
+    for j, (r, s_) in enumerate(plans):
+        if j == 0:
+            sj, img = st, (rgb,)
+        else:
+            sj = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in st.items()}
+            img = outs[j - 1]
+            with torch.cuda.stream(s_):
+                raygs.raygs_graph_capture(r.plan, raygs.make_scene(sj), *img, s_)  # reads its own copy
+            s_.synchronize()
+        sl = dict(r=r, gs=s_, st=sj, rgb=img[0])
         sl["host_rgb"] = torch.empty(sl["rgb"].shape, dtype=sl["rgb"].dtype, pin_memory=True)
-        sl["done"] = torch.cuda.Event()
-        sl["done"].record(torch.cuda.current_stream())
+        sl["rendered"], sl["read"] = torch.cuda.Event(), torch.cuda.Event()
+        sl["rendered"].record(torch.cuda.current_stream())
+        sl["read"].record(torch.cuda.current_stream())
+        slots.append(sl)
     up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def step(i):
-        sl = slots[i % 2]
-        up.wait_event(sl["done"])  # the slot's previous step is done with its inputs and image
+        sl = slots[i % len(slots)]
+        up.wait_event(sl["rendered"])  # the slot's previous graph has read its inputs
         with torch.cuda.stream(up):
             for k, v in host.items():
                 sl["st"][k].copy_(v, non_blocking=True)
         ev_in = torch.cuda.Event()
         ev_in.record(up)
         sl["gs"].wait_event(ev_in)
+        sl["gs"].wait_event(sl["read"])  # the previous image of this slot has been read back
         raygs.raygs_graph_launch(sl["r"].plan, sl["gs"])
-        ev_g = torch.cuda.Event()
-        ev_g.record(sl["gs"])
-        down.wait_event(ev_g)
+        sl["rendered"].record(sl["gs"])
+        down.wait_event(sl["rendered"])
         with torch.cuda.stream(down):
             sl["host_rgb"].copy_(sl["rgb"], non_blocking=True)
-        sl["done"].record(down)
+        sl["read"].record(down)
 
-    for i in range(4):
+    for i in range(2 * len(slots)):
         step(i)
     torch.cuda.synchronize()
-    k = max(4, min(steps, 20))
+    k = max(2 * len(slots), min(steps, 20))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(up)
     for i in range(k):
         step(i)
     e1.record(down)
     e1.synchronize()
+    torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / k
-    # leave plan 1's graph on the shared inputs again
-    with torch.cuda.stream(s1):
-        raygs.raygs_graph_capture(r1.plan, raygs.make_scene(st), *out2, s1)
-    s1.synchronize()
+    # leave the other plans' graphs on the shared inputs again
+    for j, (r, s_) in enumerate(plans[1:], start=1):
+        with torch.cuda.stream(s_):
+            raygs.raygs_graph_capture(r.plan, raygs.make_scene(st), *outs[j - 1], s_)
+        s_.synchronize()
     return ms
 
 
@@ -914,7 +925,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="profile mode: tile shape WxH (default 16x16)")
     ap.add_argument("--mode", default="bench", choices=["bench", "profile"])
-    ap.add_argument("--in-flight", type=int, default=2,
+    ap.add_argument("--in-flight", type=int, default=3,
                     help="batches in flight on separate streams (each with its own plan)")
     ap.add_argument("--workload", default="stereo", choices=["stereo", "mip720", "mip720exact", "backward"],
                     help="profile mode only: mip720exact = the 720p workload with the exact anti-aliasing; "
