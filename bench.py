@@ -83,23 +83,30 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling (every 20 ms) around the timed region: started
+    before the warm-up, so that it is running when the timed region begins; mark() brackets
+    the timed region and summary() keeps the samples taken inside it (all of them if none
+    fall inside)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, index=0, path=None):
         import tempfile
         self.index = index
         self.proc = None
+        self.window = None
         self.path = path or os.path.join(tempfile.gettempdir(), f"raygs_clocks_{os.getpid()}.csv")
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -117,24 +124,25 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                t = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
+        use = inside or rows
+        if not use:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
-        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
-                    samples=len(sm))
+        reasons = {n for r in use for n, v in zip(names, r[3]) if v.lower().startswith("active")}
+        return dict(sm_mhz=statistics.median(r[1] for r in use), sm_max_mhz=max(r[2] for r in use),
+                    reasons=sorted(reasons), samples=len(use), samples_in_timed_region=len(inside))
 
 
 def dist_setup():
@@ -388,17 +396,21 @@ def run_ours(args, world, rank, local):
         ev1.synchronize()
         return ev0.elapsed_time(ev1)
 
-    # one batch at a time (context)
-    headline(1, args.warmup)
-    single_ms = max_over_ranks(headline(1, args.steps) / args.steps, world)
-    # headline: W warm-up steps, K timed, barrier + sync on both sides
-    headline(len(plans), args.warmup)
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
+    # the clock sampler starts here, so that nvidia-smi is sampling when the timed region
+    # begins; it keeps its samples inside the timed region
     with ClockSampler(local, args.clocks_csv) as clk:
+        # one batch at a time (context)
+        headline(1, args.warmup)
+        single_ms = max_over_ranks(headline(1, args.steps) / args.steps, world)
+        # headline: W warm-up steps, K timed, barrier + sync on both sides
+        headline(len(plans), args.warmup)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        t_start = time.time()
         elapsed = headline(len(plans), args.steps)
         torch.cuda.synchronize()
+        clk.mark(t_start, time.time())
         barrier(world)
     ms = elapsed / args.steps
     ms_max = max_over_ranks(ms, world)
