@@ -450,11 +450,11 @@ def run_ours(args, world, rank, local):
     prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
     bin_bytes = binning_bytes(ctr, n * len(cams))
     # kernels per pass: preprocess (2), depth sort (4 passes x 5), row-count scan (3),
-    # row spans (1), tile-row instance scan (1), tile-row sort (passes x 5), tile-row
-    # ranges (1), chunk scan + chunk counts + instance lists (3), rasteriser (1)
+    # row spans (1), tile-row scan (1), tile-row sort (passes x 5), chunk scan + chunk
+    # counts + instance lists (3), rasteriser (1)
     trows = sum(-(-c["height"] // r.cfg.tile_h) for c in cams)
     row_passes = (max(1, (trows - 1).bit_length()) + 7) // 8
-    gpu_launches = args.steps * (2 + 20 + 3 + 1 + 1 + 5 * row_passes + 1 + 3 + 1)
+    gpu_launches = args.steps * (2 + 20 + 3 + 1 + 1 + 5 * row_passes + 3 + 1)
 
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -813,16 +813,16 @@ def binning_bytes(ctr, pairs):
     """Algorithmic bytes of one binning pass (each array read or written once per use; the
     row payload as stored): depth sort (the dense 4-B keys read, then 8 B per visible pair
     per pass in and out, the upsweeps' key reads, the last pass's 8-B rectangle gather),
-    support rows (the 32-B support sector per pair, 16 B written per row), the tile-row
-    sort (4-B key + 8-B payload + 4-B length read per row in the first pass, 12 B written per
-    kept row, 24 B per kept row in the second pass, the upsweeps' key reads), the tile-row
-    ranges and chunk counts (the sorted keys read twice), and the expansion (8-B payload read
-    per kept row, 4 B written per instance)."""
+    support rows (the 32-B support sector per pair, 12 B written per row), the tile-row
+    sort (4-B key + 8-B payload read per row in the first pass, 12 B written per kept row,
+    24 B per kept row in the second pass, the upsweeps' key reads), the chunk counts (the
+    4-B column half of each sorted payload), and the expansion (8-B payload read per kept
+    row, 4 B written per instance)."""
     nv, nr, nk, ni = (int(ctr[k]) for k in ("n_visible", "n_rows", "n_rows_kept", "n_instances"))
     depth = 4 * pairs + 8 * nv + 3 * 16 * nv + 8 * nv + 4 * pairs + 3 * 4 * nv
-    rows = 32 * nv + 16 * nr
-    row_sort = 16 * nr + 12 * nk + 24 * nk + 4 * nr + 4 * nk
-    ranges = 2 * 4 * nk
+    rows = 32 * nv + 12 * nr
+    row_sort = 12 * nr + 12 * nk + 24 * nk + 4 * nr + 4 * nk
+    ranges = 4 * nk
     expand = 8 * nk + 4 * ni
     return depth + rows + row_sort + ranges + expand
 

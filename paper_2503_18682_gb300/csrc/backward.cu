@@ -27,7 +27,7 @@ __device__ __forceinline__ uint32_t emission_index(const BackParams &P, uint32_t
   const uint32_t pair = P.pairs[pos];
   const uint2 rc = P.rect[pair];
   const uint32_t rs = P.row_off[pos] + (ty - (rc.x >> 16));
-  const uint32_t txa = P.seg[rs].y >> 16;
+  const uint32_t txa = P.seg[rs].y & 0xFFFFu;
   return P.seg_off[rs] + (tx - txa);
 }
 

@@ -149,11 +149,7 @@ struct SortVal {
 template <>
 struct SortVal<true> {
   using T = uint2;
-  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) {
-    if (!p.filter) return p.wvals_in[idx];
-    const uint2 sg = p.seg[idx];
-    return make_uint2(sg.x, (sg.y >> 16) | (p.seg_len[idx] << 16));
-  }
+  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) { return p.wvals_in[idx]; }
   static __device__ __forceinline__ void store(const SortPass &p, uint32_t dst, T v) { p.wvals_out[dst] = v; }
 };
 
@@ -559,14 +555,18 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   __shared__ uint32_t s_off[kEmitTile + 1];
   __shared__ uint32_t s_pair[kEmitTile + 1];
   __shared__ uint16_t s_owner[kEmitTile];     // the tile's pair (local index) of each row
-  __shared__ uint32_t s_trow[kTrowsShared];  // this CTA's instances per tile row
-  const bool shared_trows = R.trows <= kTrowsShared;
-  if (shared_trows)
-    for (int i = threadIdx.x; i < R.trows; i += blockDim.x) s_trow[i] = 0u;
+  // this CTA's instances (low 40 bits) and non-empty rows (high 24 bits) per tile row
+  __shared__ unsigned long long s_trow[kTrowsShared];
   const uint32_t total = R.counters->n_rows_clamped;
   const unsigned long long total_all = R.counters->n_rows;
   const uint32_t nvis = R.counters->n_visible;
   const uint32_t ntile = (total + kEmitTile - 1) / kEmitTile;
+  // shared totals while this CTA's rows fit the 24-bit row field (then a tile row's
+  // instances, at most 65,535 per row, fit the 40-bit field)
+  const bool shared_trows = R.trows <= kTrowsShared &&
+                            uint64_t((ntile + gridDim.x - 1) / gridDim.x) * kEmitTile < (1ull << 24);
+  if (shared_trows)
+    for (int i = threadIdx.x; i < R.trows; i += blockDim.x) s_trow[i] = 0ull;
   const unsigned long long ntile_all = (total_all + kEmitTile - 1) / kEmitTile;
   for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
     const uint32_t e0 = t * kEmitTile, e1 = min(e0 + uint32_t(kEmitTile), total);
@@ -640,13 +640,18 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
             }
           }
         }
-        R.seg[e] = make_uint2(p_lo + uint32_t(a), ty | (xa_t << 16));
-        R.seg_len[e] = empty ? 0u : xb_t - xa_t + 1;
+        const uint32_t len = empty ? 0u : xb_t - xa_t + 1;
+        R.seg[e] = make_uint2(p_lo + uint32_t(a), xa_t | (len << 16));  // the sort's payload as is
+        if (R.seg_len) R.seg_len[e] = len;
         R.row_key[e] = empty ? kCulled : uint32_t(cam.trow_base) + ty;
         if (!empty) {
           const uint32_t grow = uint32_t(cam.trow_base) + ty, len = xb_t - xa_t + 1;
-          if (shared_trows) atomicAdd(&s_trow[grow], len);
-          else atomicAdd(&R.trow_inst[grow], (unsigned long long)len);
+          if (shared_trows) {
+            atomicAdd(&s_trow[grow], (unsigned long long)len + (1ull << 40));
+          } else {
+            atomicAdd(&R.trow_inst[grow], (unsigned long long)len);
+            atomicAdd(&R.trow_ranges[grow].y, 1u);
+          }
         }
       }
     }
@@ -654,45 +659,14 @@ __global__ void __launch_bounds__(256) rows_kernel(RowsParams R) {
   }
   if (shared_trows)
     for (int i = threadIdx.x; i < R.trows; i += blockDim.x)
-      if (s_trow[i]) atomicAdd(&R.trow_inst[i], (unsigned long long)s_trow[i]);
+      if (s_trow[i]) {
+        atomicAdd(&R.trow_inst[i], s_trow[i] & ((1ull << 40) - 1ull));
+        atomicAdd(&R.trow_ranges[i].y, uint32_t(s_trow[i] >> 40));
+      }
 }
 
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st) {
   rows_kernel<<<G, 256, 0, st>>>(R);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------- tile ranges
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges) {
-  const uint32_t n = *d_n;
-  const uint32_t nq = (n + 3) / 4;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-    const uint32_t i0 = 4 * q;
-    uint32_t k[4];
-    if (i0 + 3 < n) {
-      uint4 v = *reinterpret_cast<const uint4 *>(keys + i0);
-      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0xFFFFFFFFu;
-    }
-    uint32_t prev = i0 == 0 ? 0xFFFFFFFFu : keys[i0 - 1];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t i = i0 + j;
-      if (i >= n) break;
-      if (i == 0 || prev != k[j]) {
-        ranges[k[j]].x = i;
-        if (i > 0) ranges[prev].y = i;
-      }
-      if (i == n - 1) ranges[k[j]].y = n;
-      prev = k[j];
-    }
-  }
-}
-
-cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st) {
-  ranges_kernel<<<G, 256, 0, st>>>(keys, d_n, ranges);
   return cudaGetLastError();
 }
 
@@ -704,13 +678,28 @@ __device__ __forceinline__ const DevCam &view_of_trow(const ExpandParams &E, int
   return E.cams[v];
 }
 
-// Exclusive scan of the per-tile-row instance totals in place (one block; 64-bit running
-// sums): each tile row's first instance, the instance total, its capacity clamp and the
-// overflow flag.
-__global__ void __launch_bounds__(1024) trow_scan_kernel(unsigned long long *v, int n, Counters *c, uint32_t cap) {
+// Exclusive scans of the per-tile-row totals (one block): the instance totals in place
+// (64-bit running sums: each tile row's first instance, the instance total, its capacity
+// clamp and the overflow flag), and the non-empty row counts into each tile row's range of
+// rows in the tile-row sort's output (rows of a tile row are contiguous there, the sort
+// being stable by tile row).
+__global__ void __launch_bounds__(1024) trow_scan_kernel(unsigned long long *v, uint2 *ranges, int n, Counters *c,
+                                                         uint32_t cap) {
   __shared__ unsigned long long ws[32];
+  __shared__ uint32_t rws[33];
   const int per = (n + 1023) / 1024;
   const int b = min(n, int(threadIdx.x) * per), e = min(n, b + per);
+  {
+    uint32_t rs = 0;
+    for (int i = b; i < e; ++i) rs += ranges[i].y;
+    uint32_t rtot;
+    uint32_t rrun = block_excl_scan(rs, rws, &rtot);
+    for (int i = b; i < e; ++i) {
+      const uint32_t k = ranges[i].y;
+      ranges[i] = make_uint2(rrun, rrun + k);
+      rrun += k;
+    }
+  }
   unsigned long long s = 0;
   for (int i = b; i < e; ++i) s += v[i];
   // block exclusive scan of s (warp scans of 64-bit values, then of the warp totals)
@@ -747,8 +736,9 @@ __global__ void __launch_bounds__(1024) trow_scan_kernel(unsigned long long *v, 
   }
 }
 
-cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st) {
-  trow_scan_kernel<<<1, 1024, 0, st>>>(trow_inst, trows, c, cap);
+cudaError_t launch_trow_scan(unsigned long long *trow_inst, uint2 *trow_ranges, int trows, Counters *c, uint32_t cap,
+                             cudaStream_t st) {
+  trow_scan_kernel<<<1, 1024, 0, st>>>(trow_inst, trow_ranges, trows, c, cap);
   return cudaGetLastError();
 }
 

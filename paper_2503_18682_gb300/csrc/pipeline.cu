@@ -233,12 +233,14 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   R.tile_w = w.cfg.tile_w;
   R.tile_h = w.cfg.tile_h;
   R.seg = w.at<uint2>(w.L.seg);
-  R.seg_len = w.at<uint32_t>(w.L.seg_len);
+  R.seg_len = w.cfg.enable_backward ? w.at<uint32_t>(w.L.seg_len) : nullptr;
   R.row_key = w.at<uint32_t>(w.L.rk[0]);
   R.trow_inst = w.at<unsigned long long>(w.L.trinst);
   R.trows = int(w.trows);
+  R.trow_ranges = w.at<uint2>(w.L.trange);
   if ((e = cudaMemsetAsync(R.trow_inst, 0, sizeof(unsigned long long) * size_t(w.trows), st)) != cudaSuccess)
     return e;
+  if ((e = cudaMemsetAsync(R.trow_ranges, 0, sizeof(uint2) * size_t(w.trows), st)) != cudaSuccess) return e;
   if ((e = launch_rows(R, w.G, st)) != cudaSuccess) return e;
   ScanJob J2{};
   J2.cnt = R.seg_len;
@@ -255,7 +257,7 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   const bool emission = w.cfg.enable_backward != 0;
   if (emission && (e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
   // first instance of every tile row, the instance total and the capacity check
-  if ((e = launch_trow_scan(R.trow_inst, int(w.trows), ctr, cap, st)) != cudaSuccess) return e;
+  if ((e = launch_trow_scan(R.trow_inst, R.trow_ranges, int(w.trows), ctr, cap, st)) != cudaSuccess) return e;
   // 3. stable sort of the non-empty rows by global tile row (8-bit digits); the first
   // pass drops the empty rows and gathers each row's payload
   const int rbits = tile_sort_bits(w.trows);
@@ -277,18 +279,15 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
     sp.G = w.G;
     sp.d_total = pass == 0 ? &ctr->n_rows_kept : nullptr;
     sp.wide = 1;
-    sp.wvals_in = w.at<uint2>(w.L.rv[cur]);
+    sp.wvals_in = pass == 0 ? R.seg : w.at<uint2>(w.L.rv[cur]);
     sp.wvals_out = w.at<uint2>(w.L.rv[dst]);
-    sp.seg = R.seg;
-    sp.seg_len = R.seg_len;
     if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
     cur = dst;
   }
   w.s2_rows = cur;
   // 4. tile-row ranges of the sorted rows, instances per tile, tile offsets, lists
-  uint2 *trange = w.at<uint2>(w.L.trange);
-  if ((e = cudaMemsetAsync(trange, 0, sizeof(uint2) * size_t(w.trows), st)) != cudaSuccess) return e;
-  if ((e = launch_ranges(w.at<uint32_t>(w.L.rk[cur]), &ctr->n_rows_kept, trange, w.G, st)) != cudaSuccess) return e;
+  // (each tile row's range of sorted rows came from the tile-row scan above)
+  uint2 *trange = R.trow_ranges;
   ExpandParams X{};
   X.cams = R.cams;
   X.n_views = w.n_views;

@@ -184,12 +184,10 @@ struct SortPass {
   int G;
   uint32_t *d_total;        // receives the number of items kept (nullable)
   // wide mode (tile-row sort of the support rows): 8-byte values (sorted pair position,
-  // first tile column | run length << 16); the filter pass reads them from seg / seg_len
+  // first tile column | run length << 16), as the row pass writes them
   int wide;
   const uint2 *wvals_in;
   uint2 *wvals_out;
-  const uint2 *seg;
-  const uint32_t *seg_len;
   // when set, the pass writes each item's tile-row count (from its pair's rectangle) in
   // place of its key (the last depth pass: the keys are not needed after it)
   const uint2 *row_rect;
@@ -222,13 +220,16 @@ struct RowsParams {
   const Counters *counters;
   int n;                    // primitives per view
   int tile_w, tile_h;
-  uint2 *seg;               // per row: (sorted pair position, ty | txa << 16)
-  uint32_t *seg_len;        // per row: tiles of the row inside the support
+  uint2 *seg;               // per row: (sorted pair position, txa | len << 16), len the tiles
+                            // of the row inside the support (the tile-row sort's payload)
+  uint32_t *seg_len;        // per row: len again, for the emission-offset scan (backward
+                            // plans only; nullable)
   uint32_t *row_key;        // per row: global tile row, or kCulled when the run is empty
   unsigned long long *trow_inst;  // [tile rows] instances of each tile row (accumulated)
+  uint2 *trow_ranges;             // [tile rows] .y: non-empty rows of each tile row (accumulated)
   int trows;
 };
-constexpr int kTrowsShared = 4096;  // tile rows whose instance totals a CTA keeps in shared memory
+constexpr int kTrowsShared = 2048;  // tile rows whose totals a CTA keeps in shared memory
 
 // Per-tile-row passes over the support rows sorted by tile row (stable, so each tile row
 // lists its rows in depth order): per-tile instance counts, then the instance lists.
@@ -330,8 +331,8 @@ cudaError_t launch_preprocess(const PrepParams &P, int num_sms, cudaStream_t st)
 cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st);
 cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st);
 cudaError_t launch_rows(const RowsParams &R, int G, cudaStream_t st);
-cudaError_t launch_ranges(const uint32_t *keys, const uint32_t *d_n, uint2 *ranges, int G, cudaStream_t st);
-cudaError_t launch_trow_scan(unsigned long long *trow_inst, int trows, Counters *c, uint32_t cap, cudaStream_t st);
+cudaError_t launch_trow_scan(unsigned long long *trow_inst, uint2 *trow_ranges, int trows, Counters *c, uint32_t cap,
+                             cudaStream_t st);
 cudaError_t launch_expand(const ExpandParams &E, cudaStream_t st);
 int expand_chunk_rows(int64_t cap, int max_tiles_x);
 int64_t expand_max_chunks(int64_t trows, int64_t cap, int chunk_rows);
