@@ -133,7 +133,11 @@ class ClockSampler:
                 continue
             try:
                 t = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                rows.append((t, float(f[1]), float(f[2]), f[5:9]))
+                try:
+                    pw = float(f[3])
+                except ValueError:
+                    pw = float("nan")
+                rows.append((t, float(f[1]), float(f[2]), f[5:9], pw))
             except ValueError:
                 continue
         inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
@@ -141,8 +145,10 @@ class ClockSampler:
         if not use:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
         reasons = {n for r in use for n, v in zip(names, r[3]) if v.lower().startswith("active")}
+        pw = [r[4] for r in use if r[4] == r[4]]
         return dict(sm_mhz=statistics.median(r[1] for r in use), sm_max_mhz=max(r[2] for r in use),
-                    reasons=sorted(reasons), samples=len(use), samples_in_timed_region=len(inside))
+                    reasons=sorted(reasons), samples=len(use), samples_in_timed_region=len(inside),
+                    power_w=statistics.median(pw) if pw else None)
 
 
 def dist_setup():
@@ -436,8 +442,14 @@ def run_ours(args, world, rank, local):
     stream.synchronize()
     e2e_single_ms = max_over_ranks(timed(e2e_step, max(2, min(args.steps, 10))), world)
     e2e_ms = e2e_single_ms
+    e2e_clocks = None
     if len(plans) >= 2:
-        e2e_ms = max_over_ranks(e2e_pipelined(plans, plan_outputs, st, rgb, host, args.steps, dev), world)
+        # clocks during the pipelined end-to-end run too (it follows the headline at full load)
+        with ClockSampler(local) as eclk:
+            t0 = time.time()
+            e2e_ms = max_over_ranks(e2e_pipelined(plans, plan_outputs, st, rgb, host, args.steps, dev), world)
+            eclk.mark(t0, time.time())
+        e2e_clocks = eclk.summary()
 
     # roofline of the dominant kernel (the rasteriser: plain FP32 ALU work)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -492,7 +504,8 @@ def run_ours(args, world, rank, local):
         clocks=clocks,
         e2e=dict(value=1e3 / e2e_ms, unit=UNIT, h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
                  ms_per_step=e2e_ms, batches_in_flight=len(plans),
-                 one_batch_at_a_time=dict(value=1e3 / e2e_single_ms, ms_per_step=e2e_single_ms)),
+                 one_batch_at_a_time=dict(value=1e3 / e2e_single_ms, ms_per_step=e2e_single_ms),
+                 clocks=e2e_clocks),
         gpu_launches=int(gpu_launches),
     )
     def context(key, fn):
