@@ -332,17 +332,34 @@ __global__ void __launch_bounds__(256) hist_offsets_kernel(uint32_t *hist, int n
   }
 }
 
-cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
-  if (p.bits != 8) return cudaErrorInvalidValue;  // every pass uses 8-bit digits
-  const int n = 256 * p.G;
+// One LSD pass: 8-bit digits over item ids (the depth sort), 4 to 8 bits over support
+// rows (the tile-row sort).
+template <int BITS, bool WIDE>
+static void sort_pass(const SortPass &p, cudaStream_t st) {
+  const int n = (1 << BITS) * p.G;
   const int nb = (n + kHistBlock - 1) / kHistBlock;
   uint32_t *bsum = p.hist + n;  // scratch after the histogram (the layout reserves 512*G + G)
-  sort_upsweep<8><<<p.G, kSortThreads, 0, st>>>(p);
+  sort_upsweep<BITS><<<p.G, kSortThreads, 0, st>>>(p);
   hist_reduce_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
   hist_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nb, p.d_total);
   hist_offsets_kernel<<<nb, 256, 0, st>>>(p.hist, n, bsum);
-  if (p.wide) sort_downsweep<8, true><<<p.G, kSortThreads, 0, st>>>(p);
-  else sort_downsweep<8, false><<<p.G, kSortThreads, 0, st>>>(p);
+  sort_downsweep<BITS, WIDE><<<p.G, kSortThreads, 0, st>>>(p);
+}
+
+cudaError_t launch_sort_pass(const SortPass &p, cudaStream_t st) {
+  if (!p.wide) {
+    if (p.bits != 8) return cudaErrorInvalidValue;
+    sort_pass<8, false>(p, st);
+  } else {
+    switch (p.bits) {
+      case 4: sort_pass<4, true>(p, st); break;
+      case 5: sort_pass<5, true>(p, st); break;
+      case 6: sort_pass<6, true>(p, st); break;
+      case 7: sort_pass<7, true>(p, st); break;
+      case 8: sort_pass<8, true>(p, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 // by the plan API (caller-owned workspace) and the allocation-free entry point.
 #include <cmath>
 
+#include <algorithm>
+
 #include "raygs_internal.cuh"
 
 namespace raygs {
@@ -258,10 +260,13 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   if (emission && (e = launch_scan(J2, w.G, st)) != cudaSuccess) return e;
   // first instance of every tile row, the instance total and the capacity check
   if ((e = launch_trow_scan(R.trow_inst, R.trow_ranges, int(w.trows), ctr, cap, st)) != cudaSuccess) return e;
-  // 3. stable sort of the non-empty rows by global tile row (8-bit digits); the first
-  // pass drops the empty rows and gathers each row's payload
+  // 3. stable sort of the non-empty rows by global tile row (at most 8-bit digits); the first
+  // pass drops the empty rows and reads each row's payload as the row pass wrote it
   const int rbits = tile_sort_bits(w.trows);
   const int rpasses = (rbits + 7) / 8;
+  // digits of equal width (at least 4 bits): the first pass scatters into fewer buckets
+  // (64 instead of 256 for 12-bit tile rows), so its output runs are longer
+  const int rdigit = std::max(4, (rbits + rpasses - 1) / rpasses);
   cur = 0;
   for (int pass = 0; pass < rpasses; ++pass) {
     SortPass sp{};
@@ -272,8 +277,8 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
     sp.vals_out = nullptr;
     sp.d_count = pass == 0 ? &ctr->n_rows_clamped : &ctr->n_rows_kept;
     sp.count_max = cap;
-    sp.shift = 8 * pass;
-    sp.bits = 8;
+    sp.shift = rdigit * pass;
+    sp.bits = rdigit;
     sp.filter = pass == 0 ? 1 : 0;
     sp.hist = hist;
     sp.G = w.G;

@@ -178,7 +178,7 @@ struct SortPass {
   const uint32_t *d_count;  // device item count (nullable: count_max is used)
   uint32_t count_max;
   int shift;
-  int bits;                 // digit width of this pass (8)
+  int bits;                 // digit width of this pass (8 for item ids, 4-8 for support rows)
   int filter;               // drop kCulled keys; value = item index
   uint32_t *hist;           // [512][G]
   int G;
