@@ -457,9 +457,10 @@ def run_ours(args, world, rank, local):
     peak_tf = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     ach_tf = flops / (stages["render_ms"] * 1e-3) / 1e12
     # HBM view of the vertex stage: attributes read once; per visible pair the 64-B record,
-    # 8-B tile rectangle and 32-B support sector written; the 4-B key of every pair
+    # 8-B tile rectangle, 1-B tile-row count and 32-B support sector written; the 4-B key of
+    # every pair
     attr_bytes = sum(v.numel() * v.element_size() for v in st.values() if hasattr(v, "numel"))
-    prep_bytes = attr_bytes + 4 * n * len(cams) + 104 * ctr["n_visible"]
+    prep_bytes = attr_bytes + 4 * n * len(cams) + 105 * ctr["n_visible"]
     bin_bytes = binning_bytes(ctr, n * len(cams))
     # kernels per pass: preprocess (2), depth sort (4 passes x 5), row-count scan (3),
     # row spans (1), tile-row scan (1), tile-row sort (passes x 5), chunk scan + chunk
@@ -824,15 +825,15 @@ def precision_ablation(args, dev):
 
 def binning_bytes(ctr, pairs):
     """Algorithmic bytes of one binning pass (each array read or written once per use; the
-    row payload as stored): depth sort (the dense 4-B keys read, then 8 B per visible pair
-    per pass in and out, the upsweeps' key reads, the last pass's 8-B rectangle gather),
+    row payload as stored): depth sort (the dense 4-B keys and 1-B tile-row counts read,
+    then 8 B per visible pair per pass in and out, the upsweeps' key reads),
     support rows (the 32-B support sector per pair, 12 B written per row), the tile-row
     sort (4-B key + 8-B payload read per row in the first pass, 12 B written per kept row,
     24 B per kept row in the second pass, the upsweeps' key reads), the chunk counts (the
     4-B column half of each sorted payload), and the expansion (8-B payload read per kept
     row, 4 B written per instance)."""
     nv, nr, nk, ni = (int(ctr[k]) for k in ("n_visible", "n_rows", "n_rows_kept", "n_instances"))
-    depth = 4 * pairs + 8 * nv + 3 * 16 * nv + 8 * nv + 4 * pairs + 3 * 4 * nv
+    depth = 5 * pairs + 8 * nv + 3 * 16 * nv + 4 * pairs + 3 * 4 * nv
     rows = 32 * nv + 12 * nr
     row_sort = 12 * nr + 12 * nk + 24 * nk + 4 * nr + 4 * nk
     ranges = 4 * nk

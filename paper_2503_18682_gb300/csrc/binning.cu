@@ -143,7 +143,14 @@ __global__ void __launch_bounds__(1024) scan_single_cta(uint32_t *data, int n, u
 template <bool WIDE>
 struct SortVal {
   using T = uint32_t;
-  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) { return p.filter ? idx : p.vals_in[idx]; }
+  // the first pass materialises the item id, with the pair's tile-row count packed above it
+  static __device__ __forceinline__ T load(const SortPass &p, uint32_t idx) {
+    if (!p.filter) return p.vals_in[idx];
+    if (!p.row_cnt8 || p.id_bits >= 32) return idx;
+    const uint32_t field = 0xFFFFFFFFu >> p.id_bits;
+    const uint32_t c = p.row_cnt8[idx];
+    return idx | ((c < 255u && c < field ? c : field) << p.id_bits);
+  }
   static __device__ __forceinline__ void store(const SortPass &p, uint32_t dst, T v) { p.vals_out[dst] = v; }
 };
 template <>
@@ -266,14 +273,24 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
       uint32_t d = (k >> p.shift) & (R - 1);
       uint32_t dst = s_base[d] + j - s_tpre[d];
       uint32_t kout = k;
+      VT vout = s_vals[j];
       if constexpr (!WIDE) {
-        if (p.row_rect) {
-          const uint2 r = p.row_rect[s_vals[j]];
-          kout = (r.y >> 16) - (r.x >> 16) + 1;
+        if (p.row_rect) {  // the last depth pass: the tile-row count as key, the bare id
+          const bool packed = p.id_bits < 32;
+          const uint32_t field = packed ? 0xFFFFFFFFu >> p.id_bits : 0u;
+          const uint32_t f = packed ? vout >> p.id_bits : 0u;
+          const uint32_t id = packed ? vout & ((1u << p.id_bits) - 1u) : vout;
+          if (f < field) {
+            kout = f;
+          } else {
+            const uint2 r = p.row_rect[id];
+            kout = (r.y >> 16) - (r.x >> 16) + 1;
+          }
+          vout = id;
         }
       }
       p.keys_out[dst] = kout;
-      SortVal<WIDE>::store(p, dst, s_vals[j]);
+      SortVal<WIDE>::store(p, dst, vout);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < R; d += kSortThreads) s_base[d] += s_tot[d];
@@ -384,19 +401,39 @@ __global__ void __launch_bounds__(256) scan_reduce_kernel(ScanJob J) {
   if (threadIdx.x == 0) J.partial[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the G <= 1024 per-CTA partial sums (64-bit running total); writes the
-// total, the capacity-clamped total and the overflow flag.
-__global__ void __launch_bounds__(32) scan_partials_kernel(ScanJob J, int G) {
-  if (threadIdx.x != 0) return;
-  unsigned long long run = 0;
-  for (int i = 0; i < G; ++i) {
-    uint32_t v = J.partial[i];
-    J.partial[i] = uint32_t(min(run, 0xFFFFFFFFull));
-    run += v;
+// Exclusive scan of the G <= 1024 per-CTA partial sums (one thread each, 64-bit running
+// sums); writes the total, the capacity-clamped total and the overflow flag.
+__global__ void __launch_bounds__(1024) scan_partials_kernel(ScanJob J, int G) {
+  __shared__ unsigned long long ws[32];
+  const int t = int(threadIdx.x), lane = t & 31, warp = t >> 5;
+  const unsigned long long v = t < G ? J.partial[t] : 0ull;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  *J.d_total = run;
-  *J.d_total_clamped = run > J.cap ? J.cap : uint32_t(run);
-  if (run > J.cap) *J.d_overflow = 1u;
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long w = ws[lane];
+    unsigned long long z = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    ws[lane] = z - w;  // warps before this one
+  }
+  __syncthreads();
+  const unsigned long long excl = ws[warp] + x - v;
+  if (t < G) J.partial[t] = uint32_t(min(excl, 0xFFFFFFFFull));
+  if (t == 1023) {
+    const unsigned long long run = excl + v;  // every partial (threads >= G add 0)
+    *J.d_total = run;
+    *J.d_total_clamped = run > J.cap ? J.cap : uint32_t(run);
+    if (run > J.cap) *J.d_overflow = 1u;
+  }
 }
 
 __global__ void __launch_bounds__(256) scan_offsets_kernel(ScanJob J) {
@@ -431,7 +468,7 @@ __global__ void __launch_bounds__(256) scan_offsets_kernel(ScanJob J) {
 
 cudaError_t launch_scan(const ScanJob &J, int G, cudaStream_t st) {
   scan_reduce_kernel<<<G, 256, 0, st>>>(J);
-  scan_partials_kernel<<<1, 32, 0, st>>>(J, G);
+  scan_partials_kernel<<<1, 1024, 0, st>>>(J, G);
   scan_offsets_kernel<<<G, 256, 0, st>>>(J);
   return cudaGetLastError();
 }

@@ -92,6 +92,7 @@ Layout make_layout(int n_views, int64_t n, int64_t tiles, int64_t trows, int64_t
   L.tscan = take(2 * sizeof(unsigned long long));
   L.depth = take(4 * VN);
   L.rect = take(8 * VN);
+  L.tcnt = take(VN);
   L.ell = take(sizeof(Ell) * VN);
   L.rec = take(sizeof(Rec) * VN);
   L.recx = mip_exact ? take(sizeof(Rec) * VN) : 0;
@@ -170,6 +171,7 @@ cudaError_t run_preprocess(Work &w, const raygs_scene &scene, cudaStream_t st) {
   P.tile_h = w.cfg.tile_h;
   P.depth_key = w.at<uint32_t>(w.L.depth);
   P.rect = w.at<uint2>(w.L.rect);
+  P.trow_cnt = w.at<uint8_t>(w.L.tcnt);
   P.ell = w.at<Ell>(w.L.ell);
   P.rec = w.at<Rec>(w.L.rec);
   P.recx = w.L.recx ? w.at<Rec>(w.L.recx) : nullptr;
@@ -185,7 +187,10 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
   const uint32_t cap = uint32_t(w.cap);
   uint32_t *hist = w.at<uint32_t>(w.L.hist);
   cudaError_t e;
-  // 1. depth sort of the visible pairs: 4 passes of 8 bits over the float32 key
+  // 1. depth sort of the visible pairs: 4 passes of 8 bits over the float32 key; the values
+  // carry each pair's tile-row count above its id (bits of the largest id)
+  int id_bits = 1;
+  while (id_bits < 32 && (uint64_t(1) << id_bits) < uint64_t(VN)) ++id_bits;
   int cur = 0;
   for (int pass = 0; pass < 4; ++pass) {
     SortPass sp{};
@@ -202,6 +207,8 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
     sp.hist = hist;
     sp.G = w.G;
     sp.d_total = pass == 0 ? &ctr->n_visible : nullptr;
+    sp.row_cnt8 = pass == 0 ? w.at<uint8_t>(w.L.tcnt) : nullptr;
+    sp.id_bits = id_bits;
     sp.row_rect = pass == 3 ? w.at<uint2>(w.L.rect) : nullptr;
     if ((e = launch_sort_pass(sp, st)) != cudaSuccess) return e;
     cur = dst;

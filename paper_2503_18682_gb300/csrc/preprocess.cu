@@ -486,9 +486,10 @@ __device__ __forceinline__ void write_record_mipx(const PrepParams &P, int64_t i
   e.cy = v.hi + so.dc1;
   e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
   P.ell[idx] = e;
-  // the rectangle also in its own compact array: the last depth-sort pass and the backward
-  // gather it by pair, and at 8 bytes per pair it largely stays in L2
+  // the rectangle also in its own compact array (the backward gathers it by pair), and its
+  // tile-row count in a byte that the first depth-sort pass reads in pair order
   P.rect[idx] = make_uint2(e.r0, e.r1);
+  P.trow_cnt[idx] = uint8_t(min(so.ty1 - so.ty0 + 1, 255));
   if (write_key) P.depth_key[idx] = __float_as_uint(z);
 }
 
@@ -512,9 +513,10 @@ __device__ __forceinline__ void write_record(const PrepParams &P, int64_t idx, c
   e.cy = v.hi + so.dc1;
   e.a = so.M00; e.b = so.M01; e.d = so.M11; e.det = so.det;
   P.ell[idx] = e;
-  // the rectangle also in its own compact array: the last depth-sort pass and the backward
-  // gather it by pair, and at 8 bytes per pair it largely stays in L2
+  // the rectangle also in its own compact array (the backward gathers it by pair), and its
+  // tile-row count in a byte that the first depth-sort pass reads in pair order
   P.rect[idx] = make_uint2(e.r0, e.r1);
+  P.trow_cnt[idx] = uint8_t(min(so.ty1 - so.ty0 + 1, 255));
   if (write_key) P.depth_key[idx] = __float_as_uint(z);
 }
 

@@ -162,6 +162,7 @@ struct PrepParams {
   int tile_w, tile_h;
   uint32_t *depth_key;
   uint2 *rect;
+  uint8_t *trow_cnt;    // tile rows of each pair's rectangle, saturated at 255
   Ell *ell;
   Rec *rec;
   Rec *recx;            // second half of the exact anti-aliasing record (views with mip = 2)
@@ -188,8 +189,14 @@ struct SortPass {
   int wide;
   const uint2 *wvals_in;
   uint2 *wvals_out;
-  // when set, the pass writes each item's tile-row count (from its pair's rectangle) in
-  // place of its key (the last depth pass: the keys are not needed after it)
+  // The depth sort carries each pair's tile-row count above its id: the first pass packs
+  // min(count, field) into the bits above id_bits (row_cnt8: the dense per-pair count,
+  // saturated at 255; a full field means "not known"), and the last pass (row_rect set)
+  // writes the count in place of the key (the keys are not needed after it) and the bare id
+  // as the value, taking the count from the pair's rectangle when the field was full.
+  // id_bits = 32 leaves no field: every count comes from the rectangle.
+  const uint8_t *row_cnt8;
+  int id_bits;
   const uint2 *row_rect;
 };
 
@@ -349,7 +356,7 @@ cudaError_t launch_resolve(const float *rgb_hi, const float *T_hi, float *rgb_lo
 // ---------------------------------------------------------------- workspace
 // Byte offsets of every buffer inside one caller-owned (or library-static) workspace.
 struct Layout {
-  size_t tilectr, cams, counters, evals, tstop, tscan, depth, rect, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
+  size_t tilectr, cams, counters, evals, tstop, tscan, depth, rect, tcnt, ell, rec, recx, s1k[2], s1v[2], off, partial, rtstart,
       seg, seg_len, seg_off, rk[2], rv[2], trange, trinst, cbase, ccnt, inst, hist, ranges, deg, degc, partials, pg, total;
   uint32_t rtstart_len;
 };

@@ -66,7 +66,7 @@ def test_binning_byte_model():
     ctr = dict(n_visible=10, n_rows=30, n_rows_kept=25, n_instances=100)
     b = bench.binning_bytes(ctr, 40)
     # depth sort, support rows, tile-row sort, chunk counts and expansion, term by term
-    depth = 4 * 40 + 8 * 10 + 3 * 16 * 10 + 8 * 10 + 4 * 40 + 3 * 4 * 10
+    depth = 5 * 40 + 8 * 10 + 3 * 16 * 10 + 4 * 40 + 3 * 4 * 10
     expect = depth + (32 * 10 + 12 * 30) + (12 * 30 + 12 * 25 + 24 * 25 + 4 * 30 + 4 * 25) + 4 * 25 + (8 * 25 + 4 * 100)
     assert b == expect
     # linear in every count
