@@ -280,7 +280,8 @@ cudaError_t run_bin_sort(Work &w, cudaStream_t st) {
     sp.keys_in = w.at<uint32_t>(w.L.rk[pass == 0 ? 0 : cur]);
     sp.vals_in = nullptr;
     const int dst = pass == 0 ? 1 : 1 - cur;
-    sp.keys_out = w.at<uint32_t>(w.L.rk[dst]);
+    // (the sorted keys themselves are not read after the last pass)
+    sp.keys_out = pass + 1 < rpasses ? w.at<uint32_t>(w.L.rk[dst]) : nullptr;
     sp.vals_out = nullptr;
     sp.d_count = pass == 0 ? &ctr->n_rows_clamped : &ctr->n_rows_kept;
     sp.count_max = cap;

@@ -174,7 +174,7 @@ struct PrepParams {
 struct SortPass {
   const uint32_t *keys_in;
   const uint32_t *vals_in;
-  uint32_t *keys_out;
+  uint32_t *keys_out;       // nullable: the pass writes only the values
   uint32_t *vals_out;
   const uint32_t *d_count;  // device item count (nullable: count_max is used)
   uint32_t count_max;
