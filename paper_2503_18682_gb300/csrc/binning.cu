@@ -202,47 +202,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
     for (int r = 0; r < kSortIPT; ++r) { key[r] = nkey[r]; val[r] = nval[r]; }
     if (kPrefetch && base + kSortTile < hi) load_tile(base + kSortTile);
     __syncthreads();
-    // The first depth pass (most items culled) first packs each warp's kept items to the
-    // front of its rows, in order (through its slice of the tile's shared key/value
-    // buffers, which are free until the scatter), so that the ranking below skips the rows
-    // left empty.  (The first row pass drops few rows and ranks in place.)
-    const bool compact = !WIDE && p.filter;
-    int nrows = kSortIPT;
-    uint32_t nkept = 0;
-    if (compact) {
-      uint32_t *ck = s_keys + warp * (32 * kSortIPT);
-      VT *cv = s_vals + warp * (32 * kSortIPT);
-#pragma unroll
-      for (int r = 0; r < kSortIPT; ++r) {
-        const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
-        const bool keep = idx < hi && key[r] != kCulled;
-        const uint32_t b = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const uint32_t pos = nkept + __popc(b & lt);
-          ck[pos] = key[r];
-          cv[pos] = val[r];
-        }
-        nkept += __popc(b);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < kSortIPT; ++r) {
-        const uint32_t pos = uint32_t(r * 32 + lane);
-        if (pos < nkept) {
-          key[r] = ck[pos];
-          val[r] = cv[pos];
-        }
-      }
-      __syncwarp();
-      nrows = int((nkept + 31) >> 5);
-    }
     uint32_t vmask = 0;
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
-      if (r >= nrows) break;  // the same in every lane of the warp
       const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
+      const bool ok = idx < hi;
       const uint32_t k = key[r];
-      const bool valid = compact ? uint32_t(r * 32 + lane) < nkept : idx < hi && !(p.filter && k == kCulled);
+      const bool valid = ok && !(p.filter && k == kCulled);
       uint32_t d = (k >> p.shift) & (R - 1);
       // lanes holding the same digit: one ballot per digit bit (warp-level multi-split)
       uint32_t peers = __ballot_sync(0xffffffffu, valid);
