@@ -170,6 +170,31 @@ def test_unbounded_supports_keep_every_covered_tile(oracle_lib, tile):
         assert_parity(compare(rgb[sl][idx], T[sl][idx], orc))
 
 
+def test_tall_view_row_counts(oracle_lib):
+    """The depth sort carries each pair's tile-row count in a byte saturated at 255; a pair
+    whose rectangle spans 255 tile rows or more takes its count from the rectangle instead.
+    On a 64 x 2400 view with 8 x 8 tiles (300 tile rows) with large primitives, both kinds
+    occur; the rows the binning counts equal the rectangles' rows, and the image keeps
+    oracle parity."""
+    rng = np.random.default_rng(41)
+    n = 300
+    sc = scenes.uniform_scene(n, seed=41)
+    sc["means"] = np.stack([rng.uniform(-0.1, 0.1, n), rng.uniform(-2.0, 2.0, n),
+                            rng.uniform(1.0, 2.5, n)], axis=1).astype(np.float32)
+    sc["log_scales"] = rng.uniform(np.log(0.05), np.log(2.0), (n, 3)).astype(np.float32)
+    cam = scenes.make_camera(64, 2400, 300.0, 300.0)
+    r, _, rgb, T, nc = gpu_render(sc, [cam], tile_w=8, tile_h=8)
+    ctr = r.last_counters
+    rects = fetch(r.debug_buffer(1), 2 * n, np.uint32).reshape(-1, 2)
+    order = fetch(r.debug_buffer(3), ctr["n_visible"], np.uint32)
+    rows = np.array([rect_of(rects, int(p))[3] - rect_of(rects, int(p))[1] + 1 for p in order])
+    assert np.sum(rows >= 255) >= 1 and np.sum(rows < 255) >= 1, np.bincount(np.minimum(rows, 255))
+    assert ctr["n_rows"] == int(rows.sum())
+    pix, idx = sample_pixels(cam, 1500, seed=3)
+    orc = oracle_lib.render(sc, cam, pixels=pix)
+    assert_parity(compare(rgb[idx], T[idx], orc))
+
+
 def test_rects_match_oracle_quad(oracle_lib):
     """The GPU tile rectangle lies inside the tiles of the oracle's projected quad bounding
     box (Eq. V_ray; the GPU further intersects it with the support ellipse's box), except
