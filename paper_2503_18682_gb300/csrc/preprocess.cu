@@ -545,7 +545,9 @@ __device__ __forceinline__ int stage_for(const T mu[3], const T Rp[9], const T s
 template <int DEG, int MODE>
 __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) {
   constexpr int K3 = 3 * (DEG + 1) * (DEG + 1);
-  constexpr int SHP = K3 + 1;  // padded row
+  // padded SH row: whole 16-byte slots, an odd number of them
+  constexpr int K4 = (K3 + 3) / 4;
+  constexpr int SHP = 4 * (K4 % 2 == 1 ? K4 : K4 + 1);
   __shared__ float s_means[kPrepThreads * 3];
   // log-scales, quaternions and logits are read once, for the per-primitive constants;
   // their space then holds the list of (primitive, view) pairs
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   float *s_q = s_scratch + 3 * kPrepThreads;
   float *s_logit = s_scratch + 7 * kPrepThreads;
   uint16_t *s_list = reinterpret_cast<uint16_t *>(s_scratch);
-  __shared__ float s_sh[kPrepThreads * SHP];
+  __shared__ __align__(16) float s_sh[kPrepThreads * SHP];
   __shared__ float s_R[kPrepThreads * 9];   // rotation of each primitive
   __shared__ float s_s[kPrepThreads * 3];   // scales
   __shared__ float s_o[kPrepThreads];       // prior opacity
@@ -574,7 +576,21 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
   stage_attr(s_ls, P.log_scales, int64_t(g0) * 3, nb * 3, P.scale_dtype, 3, 0);
   stage_attr(s_q, P.quats, int64_t(g0) * 4, nb * 4, RAYGS_F32, 4, 0);
   stage_attr(s_logit, P.logits, g0, nb, P.opacity_dtype, 1, 0);
-  stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, 1);
+  // FP32 SH rows of whole 16-byte slots are copied asynchronously: the copies land while
+  // the per-primitive constants and the cull pass run, and are waited for before the full
+  // stage, the first reader (the other forms are converted on the way in)
+  const bool sh_async = P.sh_dtype == RAYGS_F32 && K3 % 4 == 0 && (reinterpret_cast<uintptr_t>(P.sh) & 15) == 0;
+  if (sh_async) {
+    const char *src = reinterpret_cast<const char *>(P.sh) + int64_t(g0) * K3 * 4;
+    for (int i = threadIdx.x; i < nb * (K3 / 4); i += blockDim.x) {
+      const int row = i / (K3 / 4), col = i - row * (K3 / 4);
+      const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(&s_sh[row * SHP + 4 * col]));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 16 * int64_t(i)) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  } else {
+    stage_attr(s_sh, P.sh, int64_t(g0) * K3, nb * K3, P.sh_dtype, K3, SHP - K3);
+  }
   __syncthreads();
 
   // per-primitive constants
@@ -660,6 +676,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
       if (keep) s_list[base + __popc(ball & ((1u << lane) - 1u))] = uint16_t(t | ((v - v0) << 8));
     }
     (void)warp;
+    if (sh_async) asm volatile("cp.async.wait_all;\n" ::: "memory");  // this thread's SH copies
     __syncthreads();
     // pass 2: the full stage on the listed pairs
     const int n_items = s_n;
@@ -700,6 +717,7 @@ __global__ void __launch_bounds__(kPrepThreads) preprocess_kernel(PrepParams P) 
     }
     __syncthreads();
   }
+  if (sh_async) asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy outlives the block
 }
 
 // FP64 vertex stage for the (view, primitive) pairs listed by preprocess_kernel.  The
