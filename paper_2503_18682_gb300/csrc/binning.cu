@@ -178,29 +178,43 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_downsweep(SortPass p) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
 
-  // keys and values of the next tile are loaded while the current one is ranked
+  // The keys of the next tile are loaded while the current one is ranked, and so are its
+  // 4-byte values; 8-byte values would not leave registers for that, so they are loaded
+  // at the start of their own tile (they are first needed after the ranking).
   uint32_t nkey[kSortIPT];
   VT nval[kSortIPT];
-  auto load_tile = [&](uint32_t base) {
+  auto load_keys = [&](uint32_t base) {
 #pragma unroll
     for (int r = 0; r < kSortIPT; ++r) {
       const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
-      const bool ok = idx < hi;
-      nkey[r] = ok ? p.keys_in[idx] : 0u;
-      nval[r] = ok ? SortVal<WIDE>::load(p, idx) : VT{};
+      nkey[r] = idx < hi ? p.keys_in[idx] : 0u;
     }
   };
-  // (the 8-byte values would not leave registers for the prefetch)
-  constexpr bool kPrefetch = !WIDE;
-  if (kPrefetch && lo < hi) load_tile(lo);
+  auto load_vals = [&](uint32_t base, VT *dst) {
+#pragma unroll
+    for (int r = 0; r < kSortIPT; ++r) {
+      const uint32_t idx = base + warp * (32 * kSortIPT) + r * 32 + lane;
+      dst[r] = idx < hi ? SortVal<WIDE>::load(p, idx) : VT{};
+    }
+  };
+  if (lo < hi) {
+    load_keys(lo);
+    if (!WIDE) load_vals(lo, nval);
+  }
   for (uint32_t base = lo; base < hi; base += kSortTile) {
     for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
     uint32_t key[kSortIPT], off[kSortIPT];
     VT val[kSortIPT];
-    if (!kPrefetch) load_tile(base);
+    if (WIDE) load_vals(base, val);
 #pragma unroll
-    for (int r = 0; r < kSortIPT; ++r) { key[r] = nkey[r]; val[r] = nval[r]; }
-    if (kPrefetch && base + kSortTile < hi) load_tile(base + kSortTile);
+    for (int r = 0; r < kSortIPT; ++r) {
+      key[r] = nkey[r];
+      if (!WIDE) val[r] = nval[r];
+    }
+    if (base + kSortTile < hi) {
+      load_keys(base + kSortTile);
+      if (!WIDE) load_vals(base + kSortTile, nval);
+    }
     __syncthreads();
     uint32_t vmask = 0;
 #pragma unroll
