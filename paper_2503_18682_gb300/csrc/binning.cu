@@ -868,10 +868,21 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(ExpandParams E) {
   const int TX = cam.tiles_x;
   for (int x = threadIdx.x; x <= TX; x += blockDim.x) s_diff[x] = 0u;
   __syncthreads();
-  for (uint32_t i = rows.x + threadIdx.x; i < rows.y; i += blockDim.x) {
-    const uint32_t pk = E.rows[i].y;
-    atomicAdd(&s_diff[pk & 0xFFFFu], 1u);
-    atomicSub(&s_diff[(pk & 0xFFFFu) + (pk >> 16)], 1u);
+  // four rows per thread at a time, their loads issued before any of their atomics
+  for (uint32_t i0 = rows.x + threadIdx.x; i0 < rows.y; i0 += 4 * blockDim.x) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t i = i0 + k * blockDim.x;
+      pk[k] = i < rows.y ? E.rows[i].y : 0u;  // 0: no tiles
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (pk[k] >> 16) {
+        atomicAdd(&s_diff[pk[k] & 0xFFFFu], 1u);
+        atomicSub(&s_diff[(pk[k] & 0xFFFFu) + (pk[k] >> 16)], 1u);
+      }
+    }
   }
   __syncthreads();
   const int per = (TX + int(blockDim.x) - 1) / int(blockDim.x);
