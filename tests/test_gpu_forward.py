@@ -80,6 +80,17 @@ def test_blob_scene_plain_sh3(oracle_lib):
     check_views(scene, cams, oracle_lib)
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_sh_degrees(oracle_lib, deg):
+    """Every SH degree against the oracle, full image: the vertex stage stages FP32 rows of
+    whole 16-byte slots (degrees 1 and 3) with asynchronous copies and the others (degrees
+    0 and 2) synchronously."""
+    scene = scenes.blob_scene(6000, seed=40 + deg, sh_degree=deg)
+    R1, t1 = scenes.look_at([1.0, 0.5, 0.0], [0.0, 0.0, 6.0])
+    cams = [scenes.make_camera(96, 64, 80.0, 80.0), scenes.make_camera(64, 80, 70.0, 70.0, R=R1, t=t1)]
+    check_views(scene, cams, oracle_lib)
+
+
 @pytest.mark.parametrize("fp64", [2, 1, 0])
 def test_near_degenerate_primitives(oracle_lib, fp64):
     """10% near-flat primitives (axis ratio > 1e3) seen from the stereo-batch poses, shrunk
